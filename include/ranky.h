@@ -1,0 +1,189 @@
+/*
+ * ranky.h -- C ABI of the GB300 (sm_103a) column-block SVD of a sparse,
+ * short-and-fat matrix (Ranky, Tugay & Gunduz Oguducu, arXiv 2009.09767).
+ *
+ * The computation (section III of the paper, Algorithm 1):
+ *   1. split A (M x N, CSC) into D column blocks A^1 .. A^D;
+ *   2. find lonely nodes (rows with no non-zero inside a block) and, in the
+ *      RandomChecker mode (Algorithm 2), insert A[m, col] = 1 at a random
+ *      column col of that block; the default TRUNCATE mode inserts nothing
+ *      and keeps only the numerically non-zero part of each block instead;
+ *   3. reduced SVD of every block, A^i = U^i S^i V^i* (Eq. 1), here through
+ *      the block cross product A^i A^i^T and a Jacobi eigensolver;
+ *   4. proxy P = [U^1 S^1 | ... | U^D S^D] and its SVD, which gives S and U
+ *      of A' (Eqs. 2-3: P P^* = A' A'^*);
+ *   5. right vectors V = A'^T U S^-1 (the paper leaves these to future work).
+ *
+ * Conventions for every entry point:
+ *   - Indices are 0-based.  CSC: col_ptr int64[N+1] (col_ptr[0] == 0,
+ *     non-decreasing, col_ptr[N] == nnz), row_idx int32[nnz] strictly
+ *     increasing inside each column, values float32 or float64[nnz].
+ *     Stored zeros are allowed and count as zeros.
+ *   - "d_" pointers are device pointers (any allocator; the caller owns
+ *     them); "h_" pointers are host pointers.  Inputs are never modified.
+ *   - All device work is enqueued on the caller's stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream).  Argument and shape
+ *     errors are returned synchronously; errors the device detects
+ *     (non-convergence) are written to the plan's status word and returned
+ *     by svd_sync().
+ *   - No exception crosses the ABI.  A plan is not thread-safe: one run at a
+ *     time per plan; different plans may run concurrently on different
+ *     streams.
+ *   - Outputs: sigma descending; U column-major M x k; V row-major N x k;
+ *     each u_i has its largest-magnitude entry positive (first one on a
+ *     tie) and v_i takes the same sign.  Singular values whose square is at
+ *     or below the rank tolerance get zero columns in V and are not counted
+ *     in *rank.
+ */
+#ifndef RANKY_H
+#define RANKY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SVD_OK = 0,
+    SVD_ERR_INVALID_ARG = 1,    /* a pointer, size or field is out of range */
+    SVD_ERR_INVALID_CSC = 2,    /* svd_check_csc found a malformed CSC */
+    SVD_ERR_OOM = 3,            /* device or pinned host allocation failed */
+    SVD_ERR_BUDGET = 4,         /* request exceeds a server's memory budget */
+    SVD_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    SVD_ERR_NOT_CONVERGED = 6,  /* a Jacobi solve used max_sweeps */
+    SVD_ERR_TIMEOUT = 7,        /* a bounded wait ran out */
+    SVD_ERR_UNSUPPORTED = 8     /* valid request outside what is built (e.g. M > 1024) */
+} svd_status;
+
+typedef enum {
+    SVD_PREC_FP64 = 0,   /* everything in FP64 */
+    SVD_PREC_MIXED = 1   /* FP32 block Jacobi rotations and SpMM; FP64 cross
+                            products, refinement, rank decision and merge */
+} svd_precision;
+
+typedef enum {
+    SVD_RANKFIX_TRUNCATE = 0,        /* no insertion; drop numerically zero block
+                                        directions (default) */
+    SVD_RANKFIX_RANDOM = 1,          /* RandomChecker, Algorithm 2 */
+    SVD_RANKFIX_NEIGHBOR = 2,        /* NeighborChecker, Algorithm 3 (not built) */
+    SVD_RANKFIX_NEIGHBOR_RANDOM = 3  /* neighbourRandomChecker, Algorithm 4 (not built) */
+} svd_rankfix;
+
+typedef enum { SVD_VALUE_F32 = 0, SVD_VALUE_F64 = 1 } svd_value_type;
+
+/* Problem description (section III: A is M x N, split into D column blocks). */
+typedef struct {
+    int32_t M;                       /* rows, 1 .. 1024 */
+    int64_t N;                       /* columns, >= 1 */
+    int64_t nnz;                     /* stored entries, >= 0 */
+    int32_t value_type;              /* svd_value_type of the values array */
+    int32_t num_blocks;              /* D, 1 .. N */
+    const int64_t* block_col_bounds; /* host, D+1 boundaries (0 = b_0 < ... <
+                                        b_D = N), copied at svd_plan; NULL =
+                                        equal widths floor(N/D), remainder to
+                                        the last block */
+    int32_t k;                       /* triplets returned, 0 = min(M, N) */
+    int32_t precision;               /* svd_precision */
+    int32_t rank_fix;                /* svd_rankfix */
+    uint64_t seed;                   /* RandomChecker key */
+    double rank_tol;                 /* > 0: absolute tolerance on singular values;
+                                        <= 0: a squared singular value (eigenvalue
+                                        of the cross product) counts when it is
+                                        above max(M, width) * eps64 * largest */
+    int32_t max_sweeps;              /* Jacobi sweep cap, <= 0 = default (40) */
+    double jacobi_tol;               /* relative off-diagonal threshold, <= 0 =
+                                        default (per precision) */
+    int32_t refine_iters;            /* mixed mode: FP64 refinement steps of each
+                                        block eigenbasis, < 0 = default (1) */
+    int32_t flags;                   /* SVD_FLAG_* */
+} svd_desc;
+
+#define SVD_FLAG_CHECK_CSC 1   /* svd_run validates the CSC first (synchronous) */
+#define SVD_FLAG_SKIP_V 2      /* do not compute V (d_V may be NULL) */
+#define SVD_FLAG_TIMING 4      /* record per-stage CUDA events (SVD_Q_STAGE_MS) */
+
+/* One RandomChecker insertion: A'[row, col] = 1.0 (Algorithm 2). */
+typedef struct {
+    int32_t row;
+    int32_t block;
+    int64_t col;
+} svd_patch;
+
+typedef struct svd_plan_s* svd_plan_t;
+
+/* Validate desc, allocate the plan and its device workspace (owned by the
+ * plan until svd_free).  *device_bytes_needed (may be NULL) receives the
+ * workspace size.  Returns SVD_ERR_INVALID_ARG / SVD_ERR_UNSUPPORTED /
+ * SVD_ERR_OOM without allocating anything on failure. */
+svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* device_bytes_needed);
+
+/* Workspace size for desc without allocating (for admission control). */
+svd_status svd_plan_bytes(const svd_desc* desc, size_t* device_bytes_needed);
+
+/* Enqueue one SVD of the CSC matrix on `stream`.
+ *   d_sigma   double[k]            singular values, descending
+ *   d_U       double[M*k]          column-major left vectors
+ *   d_V       float[N*k] (MIXED) or double[N*k] (FP64), row-major right
+ *             vectors V = A'^T U S^-1; may be NULL with SVD_FLAG_SKIP_V
+ *   d_rank    int32[1]             number of singular values above tolerance
+ *   d_patches svd_patch[D*M]       RandomChecker insertions in (block, row)
+ *             order (may be NULL when rank_fix is TRUNCATE)
+ *   d_npatches int64[1]            number of insertions (may be NULL likewise)
+ * Asynchronous; call svd_sync() (or synchronise the stream and call
+ * svd_sync()) to read device-detected errors. */
+svd_status svd_run(svd_plan_t plan, const int64_t* d_col_ptr, const int32_t* d_row_idx,
+                   const void* d_vals, double* d_sigma, double* d_U, void* d_V,
+                   int32_t* d_rank, svd_patch* d_patches, int64_t* d_npatches,
+                   void* stream);
+
+/* Same computation from HOST buffers: copies the CSC to plan-owned device
+ * memory, runs, and copies sigma, U, V (unless SVD_FLAG_SKIP_V or h_V ==
+ * NULL), rank and patches back.  Synchronous; pinned host memory makes the
+ * copies fast but is not required. */
+svd_status svd_run_host(svd_plan_t plan, const int64_t* h_col_ptr, const int32_t* h_row_idx,
+                        const void* h_vals, double* h_sigma, double* h_U, void* h_V,
+                        int32_t* h_rank, svd_patch* h_patches, int64_t* h_npatches,
+                        void* stream);
+
+/* Wait for the plan's last run and return its device-detected status. */
+svd_status svd_sync(svd_plan_t plan);
+
+/* Synchronous CSC validation (structure only): col_ptr monotone and ending at
+ * nnz, rows in [0, M) and strictly increasing inside each column. */
+svd_status svd_check_csc(int32_t M, int64_t N, int64_t nnz, const int64_t* d_col_ptr,
+                         const int32_t* d_row_idx, void* stream);
+
+/* Copy an intermediate of the last run to host memory (after svd_sync).
+ * `bytes` must equal the item's size; returns SVD_ERR_INVALID_ARG otherwise. */
+enum {
+    SVD_Q_BLOCK_BOUNDS = 1,  /* int64[D+1] column boundaries (Algorithm 1 split) */
+    SVD_Q_LONELY = 2,        /* uint8[D*M] lonely-node flags (Algorithm 1) */
+    SVD_Q_ROW_NONEMPTY = 3,  /* uint8[M] rows with a non-zero anywhere in A */
+    SVD_Q_BLOCK_RANKS = 4,   /* int32[D] numerical rank r_i of each block */
+    SVD_Q_BLOCK_SIGMA = 5,   /* double[D*M] block singular values, descending */
+    SVD_Q_BLOCK_GRAM = 6,    /* double[M*M] A^i A^i^T of block `index` (row-major) */
+    SVD_Q_PROXY_COLS = 7,    /* int64[1] R = sum r_i */
+    SVD_Q_PROXY = 8,         /* double[M*R] proxy P, column-major */
+    SVD_Q_SWEEPS = 9,        /* int32[D+1] Jacobi sweeps per block, then the merge */
+    SVD_Q_LAUNCHES = 10,     /* int64[1] kernels launched by the last run */
+    SVD_Q_MERGE_GRAM = 11,   /* double[M*M] P P^T (row-major) */
+    SVD_Q_STAGE_MS = 12,     /* float[9] stage times of the last run (SVD_FLAG_TIMING):
+                                partition+lonely, cross products, block Jacobi,
+                                block refinement, sort+proxy, P P^T, merge
+                                eigensolve, outputs, V */
+    SVD_Q_STAGE_TOTAL = 13   /* double[10]: per-stage milliseconds summed over the
+                                runs since the previous such query, then the run
+                                count; resets the sums */
+};
+svd_status svd_query(svd_plan_t plan, int32_t what, int64_t index, void* h_dst, size_t bytes);
+
+void svd_free(svd_plan_t plan);
+const char* svd_status_str(svd_status s);
+int32_t svd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RANKY_H */

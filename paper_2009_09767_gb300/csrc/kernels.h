@@ -1,0 +1,97 @@
+// kernels.h -- host-side launchers of the column-block SVD kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rk {
+
+struct PatchRec {       // matches svd_patch in include/ranky.h
+    int32_t row;
+    int32_t block;
+    int64_t col;
+};
+
+// ---- partition.cu: Algorithm 1 split + lonely scan, Algorithm 2 -------------
+// chunk_block[c] / chunk_col[c .. c+1]: column chunks that never straddle a block.
+cudaError_t launch_occupancy(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
+                             int value_type, int M, int nchunks, const int32_t* chunk_block,
+                             const int64_t* chunk_col_lo, const int64_t* chunk_col_hi,
+                             uint32_t* occ, cudaStream_t s);
+// occ: D x W words (W = ceil(M/32)).  Writes row_ne (W words), lonely (D x W),
+// and, when random != 0, patches in (block, row) order with per-block offsets.
+cudaError_t launch_lonely_patches(const uint32_t* occ, int D, int M, const int64_t* bounds,
+                                  int random, uint64_t seed, uint32_t* row_ne, uint32_t* lonely,
+                                  PatchRec* patches, int64_t* patch_ofs, PatchRec* ext_patches,
+                                  int64_t* ext_npatches, cudaStream_t s);
+
+// ---- gram.cu: Eq. 2 block cross products --------------------------------------
+// G: D x Mp x Mp FP64 (upper triangle accumulated; must be zero on entry).
+cudaError_t launch_gram(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
+                        int value_type, int Mp, int nchunks, const int32_t* chunk_block,
+                        const int64_t* chunk_col_lo, const int64_t* chunk_col_hi, double* G,
+                        cudaStream_t s);
+cudaError_t launch_gram_patches(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
+                                int value_type, int Mp, int D, const PatchRec* patches,
+                                const int64_t* patch_ofs, int max_patches, double* G, cudaStream_t s);
+// Mirror the upper triangle into the lower one, in place, for nmat matrices.
+cudaError_t launch_symmetrize(double* G, int nmat, int Mp, cudaStream_t s);
+cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_convert_f32_f64(const float* src, double* dst, int64_t n, cudaStream_t s);
+
+// ---- jacobi.cu: block two-sided Jacobi eigensolver ----------------------------
+// G (nmat x Mp x Mp, symmetric, overwritten by its diagonalised form) and
+// Vt (nmat x Mp x Mp, rows = eigenvectors on exit).  sweeps[mat] receives the
+// sweep count, negative when max_sweeps ran out.
+template <typename T>
+cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
+                          int32_t* sweeps, cudaStream_t s);
+// Sub-problem size used for an Mp x Mp matrix (Mp must be a multiple of it).
+int jacobi_pad(int M);
+
+// ---- dense.cu: FP64 batched products, refinement, sort/rank, proxy, merge ----
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, op = transpose if t*.
+cudaError_t launch_dgemm(int nb, int m, int n, int k, double alpha, const double* A, int64_t lda,
+                         int64_t strideA, int tA, const double* B, int64_t ldb, int64_t strideB,
+                         int tB, double beta, double* C, int64_t ldc, int64_t strideC,
+                         cudaStream_t s);
+// One Ogita-Aishima refinement step for nmat symmetric matrices G with
+// approximate eigenvector rows X (Mp x Mp).  Xn receives the refined rows,
+// lam the eigenvalue estimates.  W1..W3 are Mp x Mp scratch per matrix.
+cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* lam, int nmat,
+                          int Mp, double* W1, double* W2, double* W3, double* norms,
+                          cudaStream_t s);
+// Per matrix: sort eigenvalues (lam, or the diagonal of Gdiag when lam is null)
+// of the first M indices descending, rank by tolerance, write sigma
+// (sqrt(max(lam,0))) sorted, the permutation and the rank.
+// width[b] = block width (for the default tolerance), rank_tol > 0 overrides.
+cudaError_t launch_sort_rank(const double* lam, const float* lam32, const double* diag64,
+                             const float* diag32, int nmat, int M, int Mp, const int64_t* bounds,
+                             int64_t width_all, double rank_tol, double* sigma_sorted,
+                             int32_t* perm, int32_t* rank, cudaStream_t s);
+cudaError_t launch_proxy(const double* X64, const float* X32, const double* sigma_sorted,
+                         const int32_t* perm, const int32_t* rank, int D, int M, int Mp,
+                         int64_t* proxy_ofs, double* P, cudaStream_t s);
+// S = P P^T (M x M, stored Mp x Mp), split over the R columns.
+cudaError_t launch_merge_gram(const double* P, const int64_t* proxy_ofs, int D, int M, int Mp,
+                              int64_t Rmax, double* partial, int nsplit, double* S, cudaStream_t s);
+int merge_gram_splits(int M, int64_t Rmax);
+// Final sort, sign rule, outputs and the SpMM weights W = U_k S_k^-1.
+cudaError_t launch_finalize(const double* X64, const float* X32, const double* sigma_sorted,
+                            const int32_t* perm, int M, int Mp, int k, double lam_tol_abs,
+                            int64_t tol_scale, double* d_sigma, double* d_U, int32_t* d_rank,
+                            double* W64, float* W32, cudaStream_t s);
+
+// ---- spmm.cu: V = A'^T W ------------------------------------------------------
+template <typename T>
+cudaError_t launch_spmm(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
+                        int value_type, int64_t N, int k, const T* W, T* V, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spmm_patches(const PatchRec* patches, const int64_t* npatches_dev,
+                                int max_patches, int k, const T* W, T* V, cudaStream_t s);
+
+// ---- misc ---------------------------------------------------------------------
+cudaError_t launch_check_csc(int M, int64_t N, int64_t nnz, const int64_t* col_ptr,
+                             const int32_t* row_idx, int32_t* bad, cudaStream_t s);
+
+}  // namespace rk

@@ -1,0 +1,106 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+the header declares, the Python structures match the C layout, and the
+host-side argument validation answers as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2009_09767_gb300 as rk
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "ranky.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2009_09767_gb300 import _build
+    _build.build()
+    return rk.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:svd_status|void|const char\*|int32_t)\s+(svd_\w+)\s*\(", text,
+                       flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "svd_plan" in names and "svd_run" in names and "svd_free" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for code in range(9):
+        s = lib.svd_status_str(code)
+        assert s and s != b"unknown status"
+    assert lib.svd_status_str(99) == b"unknown status"
+    assert lib.svd_version() >= 1
+
+
+def test_struct_layout_matches_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(f'''
+#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",
+    sizeof(svd_desc), offsetof(svd_desc, N), offsetof(svd_desc, nnz),
+    offsetof(svd_desc, value_type), offsetof(svd_desc, num_blocks),
+    offsetof(svd_desc, block_col_bounds), offsetof(svd_desc, k),
+    offsetof(svd_desc, precision), offsetof(svd_desc, rank_fix), offsetof(svd_desc, seed),
+    offsetof(svd_desc, rank_tol), offsetof(svd_desc, max_sweeps),
+    offsetof(svd_desc, jacobi_tol), offsetof(svd_desc, refine_iters),
+    offsetof(svd_desc, flags), sizeof(svd_patch));
+  return 0;
+}}''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    D = rk.SvdDesc
+    expect = [ctypes.sizeof(D), D.N.offset, D.nnz.offset, D.value_type.offset,
+              D.num_blocks.offset, D.block_col_bounds.offset, D.k.offset, D.precision.offset,
+              D.rank_fix.offset, D.seed.offset, D.rank_tol.offset, D.max_sweeps.offset,
+              D.jacobi_tol.offset, D.refine_iters.offset, D.flags.offset,
+              ctypes.sizeof(rk.SvdPatch)]
+    assert got == expect
+
+
+def _bytes(lib, **kw):
+    d, keep = rk.make_desc(**kw)
+    out = ctypes.c_size_t(0)
+    st = lib.svd_plan_bytes(ctypes.byref(d), ctypes.byref(out))
+    return st, out.value
+
+
+def test_plan_bytes_validation(lib):
+    ok = dict(M=64, N=4096, nnz=100, num_blocks=4)
+    st, n = _bytes(lib, **ok)
+    assert st == 0 and n > 0
+    st2, n2 = _bytes(lib, **{**ok, "num_blocks": 8})
+    assert st2 == 0 and n2 > n
+    bad = [
+        {**ok, "M": 0}, {**ok, "N": 0}, {**ok, "nnz": -1}, {**ok, "num_blocks": 0},
+        {**ok, "num_blocks": 5000}, {**ok, "k": 65}, {**ok, "k": -1},
+        {**ok, "value_type": 7}, {**ok, "precision": 5}, {**ok, "rank_fix": 9},
+        {**ok, "bounds": [0, 10, 10, 20, 4096]}, {**ok, "bounds": [1, 10, 20, 30, 4096]},
+        {**ok, "bounds": [0, 10, 20, 30, 4095]},
+    ]
+    for kw in bad:
+        assert _bytes(lib, **kw)[0] == 1, kw
+    assert _bytes(lib, **{**ok, "M": 1025})[0] == 8
+    assert _bytes(lib, **{**ok, "rank_fix": "neighbor"})[0] == 8
+    assert _bytes(lib, **{**ok, "bounds": [0, 1, 2, 3, 4096]})[0] == 0
+
+
+def test_null_plan_is_rejected(lib):
+    assert lib.svd_sync(None) == 1
+    assert lib.svd_query(None, 1, 0, None, 0) == 1
+    lib.svd_free(None)

@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle
+on the same seeded inputs.
+
+Tolerances (stated for the method's output against the oracle):
+  FP64 mode   sigma relative error <= 1e-6, tiny sigma <= 1e-12 * sigma_1
+  mixed mode  sigma relative error <= 1e-4, tiny sigma <= 1e-6 * sigma_1
+  both        singular subspaces (U and V) within 1e-4 (principal-angle sine,
+              projectors for clusters)
+Integer work (block bounds, lonely flags, RandomChecker insertions) is
+compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2009_09767_gb300 as rk
+import synth
+from tests._metrics import orthonormality, sigma_check, subspace_check
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-6, 1e-12), "mixed": (1e-4, 1e-6)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    rk.load_library()  # fails loudly when the CUDA library is not built
+    torch.cuda.set_device(0)
+
+
+def run_case(case, precision, rank_fix="truncate", seed=1234, vdtype=None, bounds=None, k=0):
+    dev = torch.device("cuda")
+    vals = case.vals if vdtype is None else case.vals.astype(vdtype)
+    t_cp = torch.from_numpy(case.col_ptr).to(dev)
+    t_ri = torch.from_numpy(case.row_idx).to(dev)
+    t_v = torch.from_numpy(np.ascontiguousarray(vals)).to(dev)
+    if bounds is None and case.widths is not None:
+        bounds = np.concatenate([[0], np.cumsum(case.widths)]).astype(np.int64)
+    plan, out = rk.svd(t_cp, t_ri, t_v, case.M, case.N, case.num_blocks, precision=precision,
+                       rank_fix=rank_fix, seed=seed, bounds=bounds, k=k)
+    res = {
+        "sigma": out["sigma"].cpu().numpy(),
+        "U": out["U"].cpu().numpy(),
+        "V": out["V"].cpu().numpy().astype(np.float64),
+        "rank": out["rank"],
+        "patches": out["patches"].cpu().numpy(),
+        "patch_blocks": out["patch_blocks"].cpu().numpy(),
+        "plan": plan,
+        "vals64": np.asarray(vals, dtype=np.float64),
+    }
+    return res
+
+
+def oracle_for(case, res):
+    p = res["patches"] if len(res["patches"]) else None
+    s, U, V, sweeps = oracle.svd_csc(case.col_ptr, case.row_idx, res["vals64"], case.M, case.N, p)
+    assert sweeps > 0
+    return s, U, V
+
+
+def check_against_oracle(case, res, precision, k=None):
+    rel_tol, abs_tol = TOL[precision]
+    s_ref, U_ref, V_ref = oracle_for(case, res)
+    kk = len(res["sigma"]) if k is None else k
+    sigma_check(res["sigma"], s_ref[:kk], rel_tol, abs_tol)
+    sub_tol = 1e-4
+    subspace_check(res["U"], U_ref[:, :kk], s_ref[:kk], sub_tol)
+    # V only where sigma is above the rank tolerance
+    r = res["rank"]
+    subspace_check(res["V"][:, :min(r, kk)], V_ref[:, :min(r, kk)], s_ref[:min(r, kk)], sub_tol)
+    assert orthonormality(res["U"]) < (1e-12 if precision == "fp64" else 1e-6)
+    # sign rule on U
+    for i in range(kk):
+        col = res["U"][:, i]
+        assert col[int(np.argmax(np.abs(col)))] > 0
+    return s_ref, U_ref, V_ref
+
+
+# --------------------------------------------------------------------------
+# the small workload (64 x 4096, 4 blocks)
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_uniform(precision):
+    case = synth.small_uniform()
+    res = run_case(case, precision)
+    s_ref, _, _ = check_against_oracle(case, res, precision)
+    plan = res["plan"]
+    # Algorithm 1 split, bit exact
+    b = plan.query(rk.Q_BLOCK_BOUNDS)
+    assert b.tolist() == oracle.block_bounds(case.N, case.num_blocks).tolist()
+    # block cross products (Eq. 2) against plain summation
+    A = oracle.densify(case.col_ptr, case.row_idx, case.vals, case.M, case.N)
+    for d in range(case.num_blocks):
+        G = plan.query(rk.Q_BLOCK_GRAM, d)
+        Gr = oracle.gram_dense(A, int(b[d]), int(b[d + 1]))
+        assert np.abs(G - Gr).max() <= 1e-13 * np.abs(Gr).max()
+        # block singular values against the oracle SVD of the block
+        sb = plan.query(rk.Q_BLOCK_SIGMA)[d]
+        sref_b = oracle.svd_dense(A[:, b[d]:b[d + 1]])[0]
+        sigma_check(sb[:len(sref_b)], sref_b, TOL[precision][0], 1e-7)
+    # proxy identity (Eqs. 2-3): P P^T = A A^T
+    P = plan.query(rk.Q_PROXY)
+    AAt = A @ A.T
+    scale = np.abs(AAt).max()
+    # mixed: FP32 rotations with one FP64 refinement step of each block basis
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.abs(P @ P.T - AAt).max() <= tol * scale
+    assert np.abs(plan.query(rk.Q_MERGE_GRAM) - AAt).max() <= tol * scale
+    assert res["rank"] == int((s_ref > 1e-7 * s_ref[0]).sum())
+    assert (plan.query(rk.Q_SWEEPS) > 0).all()
+    assert plan.query(rk.Q_LAUNCHES)[0] > 5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_lonely_truncate(precision):
+    case = synth.small_lonely()
+    res = run_case(case, precision, "truncate")
+    check_against_oracle(case, res, precision)
+    plan = res["plan"]
+    b = oracle.block_bounds(case.N, case.num_blocks)
+    A = oracle.densify(case.col_ptr, case.row_idx, case.vals, case.M, case.N)
+    lon_ref, rne_ref = oracle.lonely_dense(A, b)
+    assert (plan.query(rk.Q_LONELY).astype(bool) == lon_ref).all()
+    assert (plan.query(rk.Q_ROW_NONEMPTY).astype(bool) == rne_ref).all()
+    ranks = plan.query(rk.Q_BLOCK_RANKS)
+    # 8 rows zeroed inside the second block: its numerical rank drops by 8
+    for d in range(case.num_blocks):
+        sref_b = oracle.svd_dense(A[:, b[d]:b[d + 1]])[0]
+        expect = int((sref_b > 1e-6 * sref_b[0]).sum())
+        assert ranks[d] == expect, (d, ranks[d], expect)
+    assert ranks[1] == 56
+    assert len(res["patches"]) == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_lonely_random_checker(precision):
+    case = synth.small_lonely()
+    seed = 987654321012345
+    res = run_case(case, precision, "random", seed=seed)
+    b = oracle.block_bounds(case.N, case.num_blocks)
+    A = oracle.densify(case.col_ptr, case.row_idx, case.vals, case.M, case.N)
+    lon_ref, rne_ref = oracle.lonely_dense(A, b)
+    fix = lon_ref & rne_ref[None, :]
+    expect = oracle.random_patches(fix, b, seed)
+    assert res["patches"].tolist() == expect.tolist()
+    assert len(expect) == 8
+    # each insertion lies in the lonely row's block (Algorithm 2)
+    for (m, col), d in zip(res["patches"], res["patch_blocks"]):
+        assert b[d] <= col < b[d + 1] and fix[d, m]
+    check_against_oracle(case, res, precision)
+    # after the fix every block has full row rank
+    assert (res["plan"].query(rk.Q_BLOCK_RANKS) == case.M).all()
+
+
+# --------------------------------------------------------------------------
+# ragged shapes, degenerate cases
+
+def _random_case(M, N, density, D, seed, dtype=np.float64, empty_rows=(), name="ragged"):
+    rng = np.random.default_rng(seed)
+    c = synth.random_dense_csc(rng, M, N, density, dtype=dtype, name=name)
+    c.num_blocks = D
+    if len(empty_rows):
+        c = synth.zero_rows_in_columns(c, list(empty_rows), 0, N)
+    return c
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("M,N,D,density", [
+    (50, 700, 3, 0.05),      # M not a multiple of the tile, N mod D != 0
+    (100, 999, 7, 0.03),     # several sub-problem pairs, remainder block
+    (200, 3000, 5, 0.02),    # Mp = 256: 4 pairs per step
+    (33, 40, 40, 0.3),       # one column per block
+    (7, 19, 2, 0.5),
+    (1, 10, 3, 0.5),         # a single row
+])
+def test_ragged_shapes(precision, M, N, D, density):
+    case = _random_case(M, N, density, D, seed=M * 1000 + N)
+    res = run_case(case, precision)
+    check_against_oracle(case, res, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_globally_empty_rows_and_k(precision):
+    case = _random_case(40, 500, 0.05, 4, seed=7, empty_rows=(3, 17, 39))
+    res = run_case(case, precision, k=30)
+    s_ref, _, _ = check_against_oracle(case, res, precision, k=30)
+    full = run_case(case, precision)
+    assert full["rank"] == 37  # three rows empty in all of A
+    assert np.abs(full["sigma"][37:]).max() == 0.0
+    assert np.abs(full["V"][:, 37:]).max() == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_all_zero_matrix(precision):
+    M, N = 16, 64
+    case = synth.CscCase("zero", M, N, np.zeros(N + 1, np.int64), np.zeros(0, np.int32),
+                         np.zeros(0, np.float64), 2)
+    res = run_case(case, precision)
+    assert res["rank"] == 0
+    assert np.abs(res["sigma"]).max() == 0.0
+    assert np.abs(res["V"]).max() == 0.0
+    assert orthonormality(res["U"]) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_explicit_widths_and_f32_values(precision):
+    case = _random_case(64, 2000, 0.02, 4, seed=11, dtype=np.float32)
+    bounds = np.array([0, 100, 1100, 1500, 2000], np.int64)
+    res = run_case(case, precision, bounds=bounds)
+    assert res["plan"].query(rk.Q_BLOCK_BOUNDS).tolist() == bounds.tolist()
+    check_against_oracle(case, res, precision)
+
+
+def test_run_host_matches_run():
+    case = synth.small_uniform()
+    dev = torch.device("cuda")
+    plan = rk.Plan(case.M, case.N, case.nnz, case.num_blocks, value_type="f64", precision="fp64")
+    out = rk.alloc_outputs(plan)
+    plan.run(torch.from_numpy(case.col_ptr).to(dev), torch.from_numpy(case.row_idx).to(dev),
+             torch.from_numpy(case.vals).to(dev), out["sigma"], out["U"], out["V"], out["rank"],
+             out["patches"], out["npatches"])
+    plan.sync()
+    hs = np.zeros(plan.k)
+    hU = np.zeros((plan.k, plan.M))
+    hV = np.zeros((plan.N, plan.k))
+    hr = np.zeros(1, np.int32)
+    plan.run_host(case.col_ptr, case.row_idx, case.vals, hs, hU, hV, hr)
+    # the cross products accumulate with atomics: equal up to summation order
+    np.testing.assert_allclose(hs, out["sigma"].cpu().numpy(), rtol=1e-12)
+    assert np.abs(np.abs(hU.T.T @ out["U"].cpu().numpy().T).diagonal() - 1).max() < 1e-10
+    np.testing.assert_allclose(np.abs(hV), np.abs(out["V"].cpu().numpy()), rtol=0, atol=1e-10)
+    assert hr[0] == out["rank"].item()
+
+
+def test_check_csc_rejects_malformed():
+    lib = rk.load_library()
+    dev = torch.device("cuda")
+    good_cp = torch.tensor([0, 2, 3], dtype=torch.int64, device=dev)
+    good_ri = torch.tensor([0, 2, 1], dtype=torch.int32, device=dev)
+    s = rk._stream_handle(None)
+    assert lib.svd_check_csc(3, 2, 3, rk._ptr(good_cp), rk._ptr(good_ri), s) == 0
+    unsorted = torch.tensor([2, 0, 1], dtype=torch.int32, device=dev)
+    assert lib.svd_check_csc(3, 2, 3, rk._ptr(good_cp), rk._ptr(unsorted), s) == 2
+    out_of_range = torch.tensor([0, 3, 1], dtype=torch.int32, device=dev)
+    assert lib.svd_check_csc(3, 2, 3, rk._ptr(good_cp), rk._ptr(out_of_range), s) == 2
+    bad_end = torch.tensor([0, 2, 4], dtype=torch.int64, device=dev)
+    assert lib.svd_check_csc(3, 2, 3, rk._ptr(bad_end), rk._ptr(good_ri), s) == 2
