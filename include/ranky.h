@@ -179,6 +179,38 @@ enum {
 };
 svd_status svd_query(svd_plan_t plan, int32_t what, int64_t index, void* h_dst, size_t bytes);
 
+/* Right singular vectors without any device allocation.  The paper has no
+ * counterpart: this serves callers that must not allocate device memory on
+ * their call path (services that split the GPU into fixed budgets at start-up
+ * and refuse later allocations; latency-bound callers that cannot take
+ * cudaMalloc's implicit device-wide synchronisation or its failure under
+ * memory pressure).
+ *
+ * Computes d_V = A'^T U_k S_k^-1 (row-major N x k, float32 when v_type is
+ * SVD_VALUE_F32, float64 when SVD_VALUE_F64) from a CSC matrix and the
+ * singular values d_sigma (double[k], descending) and left vectors d_U
+ * (double, column-major M x k) that svd_run returned; d_patches / d_npatches
+ * (both NULL or both set, max_patches = capacity) add RandomChecker
+ * insertions as svd_run does.  Columns whose squared singular value is at or
+ * below the rank tolerance (rank_tol^2 when rank_tol > 0, else
+ * max(M, N) * eps64 * sigma_1^2) are zero.
+ *
+ * Its scratch (the M x k weights) is a static device array of 4 MiB that
+ * every GPU loading the library keeps until the process exits:
+ * M * k * sizeof(V element) above 4 MiB returns SVD_ERR_UNSUPPORTED without
+ * enqueuing work.  All calls on a device share the array and it keeps the
+ * last call's contents; every call rewrites what it reads, but calls whose
+ * kernels overlap on the GPU race on it.  The first call on each device
+ * looks up the array's device address; make it before any stream capture.
+ * Asynchronous on `stream`; argument errors return synchronously. */
+svd_status svd_right_vectors_static(int32_t M, int64_t N, int64_t nnz, int32_t value_type,
+                                    const int64_t* d_col_ptr, const int32_t* d_row_idx,
+                                    const void* d_vals, int32_t k, const double* d_sigma,
+                                    const double* d_U, double rank_tol,
+                                    const svd_patch* d_patches, const int64_t* d_npatches,
+                                    int64_t max_patches, int32_t v_type, void* d_V,
+                                    void* stream);
+
 void svd_free(svd_plan_t plan);
 const char* svd_status_str(svd_status s);
 int32_t svd_version(void);

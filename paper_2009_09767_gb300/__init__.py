@@ -288,3 +288,25 @@ def svd(col_ptr, row_idx, vals, M, N, num_blocks, *, stream=None, plan: Plan | N
         "patch_blocks": blk,
     }
     return plan, res
+
+
+def right_vectors_static(M, N, col_ptr, row_idx, vals, sigma, U, V, *, k=None, rank_tol=0.0,
+                         patches=None, npatches=None, max_patches=0, stream=None):
+    """V = A'^T U_k S_k^-1 through svd_right_vectors_static: no device
+    allocation; the weights live in the library's static 4 MiB device array
+    (see include/ranky.h for the sharing rules)."""
+    lib = load_library()
+    f = lib.svd_right_vectors_static
+    if f.argtypes is None:
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        f.argtypes = [I32, I64, I64, I32, P, P, P, I32, P, P, ctypes.c_double, P, P, I64, I32,
+                      P, P]
+        f.restype = I32
+    import torch
+    kk = int(sigma.numel()) if k is None else int(k)
+    vt = 0 if vals.dtype == torch.float32 else 1
+    vv = 0 if V.dtype == torch.float32 else 1
+    st = f(int(M), int(N), int(row_idx.numel()), vt, _ptr(col_ptr), _ptr(row_idx), _ptr(vals), kk,
+           _ptr(sigma), _ptr(U), float(rank_tol), _ptr(patches), _ptr(npatches), int(max_patches),
+           vv, _ptr(V), _stream_handle(stream))
+    _check(st, "svd_right_vectors_static")
