@@ -104,6 +104,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic of one block-Jacobi launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), per matrix, with the hash of the kernel source it was taken on;
+# reported as null once the source changes.  See profiles/k_jacobi_f32_zipf_wide_250k.md.
+JACOBI_TRAFFIC = {"source_sha256_16": "b5bdde1ed4528738", "bytes_per_matrix": 19.917312e6 / 16}
+
+
+def source_hash(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def jacobi_flops(sweeps: np.ndarray, Mp: int) -> float:
     """Algorithmic FP32 flops of the block Jacobi launch: per sweep and matrix,
     the three panel products (rows of G, columns of G, rows of the eigenvector
@@ -299,6 +311,10 @@ def main():
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts "
                                "and maximum clock)",
                 "traffic": None, "kernel_ms": jac_ms, "algorithmic_flops": jac_flops}
+    if source_hash("paper_2009_09767_gb300/csrc/jacobi.cu") == JACOBI_TRAFFIC["source_sha256_16"]:
+        roofline["traffic"] = JACOBI_TRAFFIC["bytes_per_matrix"] * case.num_blocks
+        roofline["traffic_note"] = ("ncu dram bytes of a 16-matrix launch, scaled by matrices "
+                                    "to this launch")
     bytes_per_svd = algorithmic_bytes(case, R, plan.k, s_v)
     peaks = measured_peaks()
     hbm = {"algorithmic_bytes_per_svd": bytes_per_svd,
