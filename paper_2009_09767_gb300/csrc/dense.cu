@@ -24,7 +24,10 @@ constexpr int GT = 64, GK = 16;
 __global__ void __launch_bounds__(256)
 k_dgemm(int m, int n, int k, double alpha, const double* __restrict__ A, int64_t lda,
         int64_t strideA, int tA, const double* __restrict__ B, int64_t ldb, int64_t strideB,
-        int tB, double beta, double* __restrict__ C, int64_t ldc, int64_t strideC) {
+        int tB, double beta, double* __restrict__ C, int64_t ldc, int64_t strideC, int sym) {
+    // sym: the product is known to be symmetric (m == n): only tiles on or
+    // above the diagonal are computed and each is written to both halves.
+    if (sym && blockIdx.x < blockIdx.y) return;
     __shared__ double As[GK][GT + 1];
     __shared__ double Bs[GK][GT + 1];
     const int bz = blockIdx.z;
@@ -75,7 +78,9 @@ k_dgemm(int m, int n, int k, double alpha, const double* __restrict__ A, int64_t
             const int gj = j0 + tx + 16 * c;
             if (gj >= n) continue;
             double* cp = C + (int64_t)gi * ldc + gj;
-            *cp = beta == 0.0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * *cp;
+            const double v = beta == 0.0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * *cp;
+            *cp = v;
+            if (sym && blockIdx.x != blockIdx.y) C[(int64_t)gj * ldc + gi] = v;
         }
     }
 }
@@ -84,11 +89,12 @@ k_dgemm(int m, int n, int k, double alpha, const double* __restrict__ A, int64_t
 cudaError_t launch_dgemm(int nb, int m, int n, int k, double alpha, const double* A, int64_t lda,
                          int64_t strideA, int tA, const double* B, int64_t ldb, int64_t strideB,
                          int tB, double beta, double* C, int64_t ldc, int64_t strideC,
-                         cudaStream_t s) {
+                         cudaStream_t s, int sym) {
     if (nb <= 0 || m <= 0 || n <= 0) return cudaSuccess;
+    if (sym && m != n) return cudaErrorInvalidValue;
     dim3 grid((unsigned)ceil_div(n, GT), (unsigned)ceil_div(m, GT), (unsigned)nb);
     k_dgemm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, strideA, tA, B, ldb, strideB, tB, beta,
-                                 C, ldc, strideC);
+                                 C, ldc, strideC, sym);
     return cudaGetLastError();
 }
 
@@ -109,7 +115,7 @@ namespace {
 // The two 2-norms are estimated by power iteration on the symmetric matrices
 // (in FP32: only the magnitude matters), scaled up by 1.5 against the
 // iteration's underestimate.
-constexpr int kPowerIters = 12;
+constexpr int kPowerIters = 8;
 
 __global__ void __launch_bounds__(512)
 k_oa_norms(const double* __restrict__ W1, const double* __restrict__ W3, int Mp,
@@ -230,12 +236,12 @@ cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* 
                           int Mp, double* W1, double* W2, double* W3, double* norms,
                           cudaStream_t s) {
     const int64_t st = (int64_t)Mp * Mp;
-    // W1 = X X^T
-    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, X, Mp, st, 1, 0.0, W1, Mp, st, s));
+    // W1 = X X^T (symmetric)
+    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, X, Mp, st, 1, 0.0, W1, Mp, st, s, 1));
     // W2 = X G
     RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, G, Mp, st, 0, 0.0, W2, Mp, st, s));
-    // W3 = W2 X^T = X G X^T
-    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W2, Mp, st, 0, X, Mp, st, 1, 0.0, W3, Mp, st, s));
+    // W3 = W2 X^T = X G X^T (symmetric)
+    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W2, Mp, st, 0, X, Mp, st, 1, 0.0, W3, Mp, st, s, 1));
     k_oa_norms<<<nmat, 512, 0, s>>>(W1, W3, Mp, lam, norms);
     RK_CUDA_TRY(cudaGetLastError());
     const int bx = (int)std::min<int64_t>(ceil_div(st, 256), 1024);

@@ -22,6 +22,8 @@
 // rotate, so their eigenvectors stay exact unit vectors.
 #include <cooperative_groups.h>
 
+#include <cstdint>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,7 +33,7 @@ namespace rk {
 
 namespace {
 
-constexpr int kJT = 256;   // threads per CTA
+constexpr int kJT = 512;   // threads per CTA (16 warps)
 constexpr int kMaxCluster = 8;
 
 // circle schedule over n (even) items: partner pair u of round r
@@ -56,24 +58,58 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
+// 16-byte vectors of T
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static float get(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+};
+template <> struct V16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+};
+
+// Load four consecutive T from 16-byte aligned shared memory.
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T (&o)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 c = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = a.x; o[1] = a.y; o[2] = c.x; o[3] = c.y;
+    }
+}
+
 template <typename T, int B2>
 struct JacobiSmem {
-    static constexpr int LD = B2 + 1;            // padded sub/Q stride
-    static constexpr int TW = 4096 / B2;         // panel tile width (row update) / height (col update)
-    static constexpr int SLD = TW + 1;           // padded stage stride
+    static constexpr int b = B2 / 2;
+    static constexpr int PAD = 16 / (int)sizeof(T);  // keeps rows 16-byte aligned
+    static constexpr int LD = B2 + 1;               // sub-problem stride (odd)
+    static constexpr int QLD = B2 + PAD;            // Q stride (aligned rows)
+    static constexpr int TW = 8192 / B2;            // row-panel tile width
+    static constexpr int RSLD = TW + PAD;           // row-panel stage stride
+    static constexpr int TR = 8192 / B2;            // column-panel tile height
+    static constexpr int CSLD = B2 + 1;             // column-panel stage stride
+    static constexpr int STAGE = (B2 * RSLD > TR * CSLD) ? B2 * RSLD : TR * CSLD;
     static size_t bytes(int ppc) {
-        return sizeof(T) * ((size_t)B2 * LD * (1 + ppc) + (size_t)B2 * SLD) +
-               sizeof(T) * 3 * (B2 / 2) + sizeof(int) * 2 * (B2 / 2);
+        return sizeof(T) * ((size_t)B2 * LD + (size_t)ppc * B2 * QLD + (size_t)STAGE) +
+               sizeof(T) * 3 * b + sizeof(int) * 2 * b;
     }
 };
 
 // One cyclic sweep (B2-1 rounds) on the shared sub-matrix, accumulating Q.
-// Returns (through *rotated) whether any rotation passed the threshold.
+// Per round: b threads compute the b disjoint rotations into a table; then
+// every 2x2 block (pair u rows, pair v columns) is updated from both sides by
+// one thread, and the Q columns of each pair by (row, pair) threads.
 template <typename T, int B2>
 __device__ void inner_sweep(T* sub, T* Q, T* cs, T* sn, T* tn, int* pp, int* qq, T tol, T floor_abs,
                             int* rotated) {
-    constexpr int LD = JacobiSmem<T, B2>::LD;
-    constexpr int b = B2 / 2;
+    using S = JacobiSmem<T, B2>;
+    constexpr int LD = S::LD, QLD = S::QLD, b = S::b;
     for (int r = 0; r < B2 - 1; ++r) {
         if (threadIdx.x < b) {
             const int u = threadIdx.x;
@@ -94,7 +130,6 @@ __device__ void inner_sweep(T* sub, T* Q, T* cs, T* sn, T* tn, int* pp, int* qq,
             cs[u] = c; sn[u] = s; tn[u] = t; pp[u] = p; qq[u] = q;
         }
         __syncthreads();
-        // two-sided update, one 2x2 block (pair u rows, pair v cols) per item
         for (int it = threadIdx.x; it < b * b; it += kJT) {
             const int u = it / b, v = it % b;
             const int pu = pp[u], qu = qq[u], pv = pp[v], qv = qq[v];
@@ -120,36 +155,48 @@ __device__ void inner_sweep(T* sub, T* Q, T* cs, T* sn, T* tn, int* pp, int* qq,
             sub[qu * LD + pv] = cv * y10 - sv * y11;
             sub[qu * LD + qv] = sv * y10 + cv * y11;
         }
-        // Q <- Q R on columns p, q
+        // Q <- Q R on columns p, q; pair index fastest so a warp touches one row
         for (int it = threadIdx.x; it < b * B2; it += kJT) {
-            const int u = it / B2, row = it % B2;
+            const int u = it % b, row = it / b;
             const T s = sn[u];
             if (s == T(0)) continue;
             const T c = cs[u];
             const int p = pp[u], q = qq[u];
-            const T x = Q[row * LD + p], y = Q[row * LD + q];
-            Q[row * LD + p] = c * x - s * y;
-            Q[row * LD + q] = s * x + c * y;
+            const T x = Q[row * QLD + p], y = Q[row * QLD + q];
+            Q[row * QLD + p] = c * x - s * y;
+            Q[row * QLD + q] = s * x + c * y;
         }
         __syncthreads();
     }
 }
 
-// rows idx(0..B2-1) of M (ld = Mp) <- Q^T * rows, over all Mp columns
+// Global index of local sub-problem index k (0..B2-1) for block pair (bi, bj).
+template <int B2>
+__device__ __forceinline__ int gidx(int bi, int bj, int k) {
+    constexpr int b = B2 / 2;
+    return k < b ? bi * b + k : bj * b + (k - b);
+}
+
+// rows idx(0..B2-1) of Mat (ld = Mp) <- Q^T * rows, over all Mp columns.
+// Tile: B2 rows x TW columns staged in shared memory; each thread computes a
+// 4 x 4 block of outputs with 16-byte shared loads.
 template <typename T, int B2>
 __device__ void panel_rows(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage) {
-    constexpr int LD = JacobiSmem<T, B2>::LD;
-    constexpr int TW = JacobiSmem<T, B2>::TW;
-    constexpr int SLD = JacobiSmem<T, B2>::SLD;
-    constexpr int b = B2 / 2;
-    constexpr int CG = TW / 4;              // column groups of 4
+    using S = JacobiSmem<T, B2>;
+    constexpr int QLD = S::QLD, TW = S::TW, SLD = S::RSLD;
+    constexpr int VN = V16<T>::n;
+    using VT = typename V16<T>::type;
+    constexpr int CG = TW / 4;
     const int ti = threadIdx.x / CG, tc = threadIdx.x % CG;
+    const int i0 = ti * 4, j0 = tc * 4;
     for (int c0 = 0; c0 < Mp; c0 += TW) {
-        const int cw = min(TW, Mp - c0);
-        for (int it = threadIdx.x; it < B2 * TW; it += kJT) {
-            const int k = it / TW, c = it % TW;
-            const int g = k < b ? bi * b + k : bj * b + (k - b);
-            stage[k * SLD + c] = c < cw ? ldcg(Mat + (int64_t)g * Mp + c0 + c) : T(0);
+        const int cw = min(TW, Mp - c0);   // multiple of 32 (Mp is)
+        for (int it = threadIdx.x; it < B2 * (TW / VN); it += kJT) {
+            const int k = it / (TW / VN), c = (it % (TW / VN)) * VN;
+            VT v;
+            if (c < cw) v = __ldcg(reinterpret_cast<const VT*>(Mat + (int64_t)gidx<B2>(bi, bj, k) * Mp + c0 + c));
+            else v = VT{};
+            *reinterpret_cast<VT*>(stage + k * SLD + c) = v;
         }
         __syncthreads();
         T acc[4][4];
@@ -157,47 +204,54 @@ __device__ void panel_rows(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-        const int i0 = ti * 4, j0 = tc * 4;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < B2; ++k) {
             T qv[4], xv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) qv[i] = Q[k * LD + i0 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) xv[j] = stage[k * SLD + j0 + j];
+            lds4<T>(Q + k * QLD + i0, qv);
+            lds4<T>(stage + k * SLD + j0, xv);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += qv[i] * xv[j];
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(qv[i], xv[j], acc[i][j]);
         }
+        if (j0 < cw) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = i0 + i;
-            const int g = k < b ? bi * b + k : bj * b + (k - b);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j0 + j < cw) Mat[(int64_t)g * Mp + c0 + j0 + j] = acc[i][j];
+            for (int i = 0; i < 4; ++i) {
+                T* dst = Mat + (int64_t)gidx<B2>(bi, bj, i0 + i) * Mp + c0 + j0;
+                if constexpr (sizeof(T) == 4) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                } else {
+                    reinterpret_cast<double2*>(dst)[0] = make_double2(acc[i][0], acc[i][1]);
+                    reinterpret_cast<double2*>(dst)[1] = make_double2(acc[i][2], acc[i][3]);
+                }
+            }
         }
         __syncthreads();
     }
 }
 
-// columns idx(0..B2-1) of G <- columns * Q, over all Mp rows
+// columns idx(0..B2-1) of Mat <- columns * Q, over all Mp rows.
 template <typename T, int B2>
 __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage) {
-    constexpr int LD = JacobiSmem<T, B2>::LD;
-    constexpr int TR = JacobiSmem<T, B2>::TW;
-    constexpr int SLD = JacobiSmem<T, B2>::SLD;
-    constexpr int b = B2 / 2;
+    using S = JacobiSmem<T, B2>;
+    constexpr int QLD = S::QLD, TR = S::TR, SLD = S::CSLD;
+    constexpr int VN = V16<T>::n;
+    using VT = typename V16<T>::type;
     constexpr int JG = B2 / 4;
     const int tr = threadIdx.x / JG, tj = threadIdx.x % JG;
+    const int i0 = tr * 4, j0 = tj * 4;
     for (int r0 = 0; r0 < Mp; r0 += TR) {
         const int rh = min(TR, Mp - r0);
-        // stage transposed: stage[k][r] = Mat[r0 + r][idx(k)]
-        for (int it = threadIdx.x; it < TR * B2; it += kJT) {
-            const int r = it / B2, k = it % B2;
-            const int g = k < b ? bi * b + k : bj * b + (k - b);
-            stage[k * SLD + r] = r < rh ? ldcg(Mat + (int64_t)(r0 + r) * Mp + g) : T(0);
+        for (int it = threadIdx.x; it < TR * (B2 / VN); it += kJT) {
+            const int r = it / (B2 / VN), k = (it % (B2 / VN)) * VN;
+            if (r < rh) {
+                const VT v = __ldcg(reinterpret_cast<const VT*>(Mat + (int64_t)(r0 + r) * Mp + gidx<B2>(bi, bj, k)));
+#pragma unroll
+                for (int e = 0; e < VN; ++e) stage[r * SLD + k + e] = V16<T>::get(v, e);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VN; ++e) stage[r * SLD + k + e] = T(0);
+            }
         }
         __syncthreads();
         T acc[4][4];
@@ -205,27 +259,26 @@ __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-        const int i0 = tr * 4, j0 = tj * 4;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < B2; ++k) {
             T xv[4], qv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) xv[i] = stage[k * SLD + i0 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) qv[j] = Q[k * LD + j0 + j];
+            for (int i = 0; i < 4; ++i) xv[i] = stage[(i0 + i) * SLD + k];
+            lds4<T>(Q + k * QLD + j0, qv);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * qv[j];
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], qv[j], acc[i][j]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (i0 + i >= rh) continue;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int k = j0 + j;
-                const int g = k < b ? bi * b + k : bj * b + (k - b);
-                Mat[(int64_t)(r0 + i0 + i) * Mp + g] = acc[i][j];
+            T* dst = Mat + (int64_t)(r0 + i0 + i) * Mp + gidx<B2>(bi, bj, j0);
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            } else {
+                reinterpret_cast<double2*>(dst)[0] = make_double2(acc[i][0], acc[i][1]);
+                reinterpret_cast<double2*>(dst)[1] = make_double2(acc[i][2], acc[i][3]);
             }
         }
         __syncthreads();
@@ -233,10 +286,11 @@ __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
 }
 
 template <typename T, int B2>
-__global__ void __launch_bounds__(kJT)
+__global__ void __launch_bounds__(kJT, 1)
 k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc, int max_sweeps,
          T tol, int32_t* __restrict__ sweeps_out) {
-    constexpr int LD = JacobiSmem<T, B2>::LD;
+    using SM = JacobiSmem<T, B2>;
+    constexpr int LD = SM::LD, QLD = SM::QLD;
     constexpr int b = B2 / 2;
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
@@ -247,10 +301,10 @@ k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc
     const int npairs = nb / 2;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sub = reinterpret_cast<T*>(smem_raw);
-    T* Qs = sub + B2 * LD;
-    T* stage = Qs + (size_t)ppc * B2 * LD;
-    T* cs = stage + (size_t)B2 * JacobiSmem<T, B2>::SLD;
+    T* stage = reinterpret_cast<T*>(smem_raw);        // 16-byte aligned
+    T* Qs = stage + SM::STAGE;                            // STAGE, QLD keep alignment
+    T* sub = Qs + (size_t)ppc * B2 * QLD;
+    T* cs = sub + (size_t)B2 * LD;
     T* sn = cs + b;
     T* tn = sn + b;
     int* pp = reinterpret_cast<int*>(tn + b);
@@ -290,13 +344,11 @@ k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc
                 if (u >= npairs) break;
                 int bi, bj;
                 circle_pair(nb, step, u, bi, bj);
-                T* Q = Qs + (size_t)t * B2 * LD;
+                T* Q = Qs + (size_t)t * B2 * QLD;
                 for (int it = threadIdx.x; it < B2 * B2; it += kJT) {
                     const int i = it / B2, j = it % B2;
-                    const int gi = i < b ? bi * b + i : bj * b + (i - b);
-                    const int gj = j < b ? bi * b + j : bj * b + (j - b);
-                    sub[i * LD + j] = ldcg(G + (int64_t)gi * Mp + gj);
-                    Q[i * LD + j] = i == j ? T(1) : T(0);
+                    sub[i * LD + j] = ldcg(G + (int64_t)gidx<B2>(bi, bj, i) * Mp + gidx<B2>(bi, bj, j));
+                    Q[i * QLD + j] = i == j ? T(1) : T(0);
                 }
                 __syncthreads();
                 inner_sweep<T, B2>(sub, Q, cs, sn, tn, pp, qq, tol, floor_abs, &rot_flag);
@@ -310,7 +362,7 @@ k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc
                 if (u >= npairs) break;
                 int bi, bj;
                 circle_pair(nb, step, u, bi, bj);
-                panel_cols<T, B2>(G, Mp, bi, bj, Qs + (size_t)t * B2 * LD, stage);
+                panel_cols<T, B2>(G, Mp, bi, bj, Qs + (size_t)t * B2 * QLD, stage);
             }
             cluster.sync();
         }
@@ -331,13 +383,54 @@ k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc
     if (crank == 0 && threadIdx.x == 0) sweeps_out[mat] = converged ? sweep : -sweep;
 }
 
+// Cluster size for nmat matrices with npairs block pairs per step.  A CTA
+// handles ppc = ceil(npairs / csize) pairs per step, so a matrix takes time
+// ~ ppc; clusters run in waves of the hardware's maximum active clusters for
+// that size.  Choose the size with the fewest waves * ppc (ties: the larger
+// cluster, lower latency per matrix).
+template <typename T, int B2>
+int pick_cluster(int nmat, int npairs) {
+    auto kern = k_jacobi<T, B2>;
+    int best = 1;
+    int64_t best_cost = INT64_MAX;
+    for (int cs = 1; cs <= kMaxCluster && cs <= npairs; cs *= 2) {
+        const int ppc = (npairs + cs - 1) / cs;
+        const size_t smem = JacobiSmem<T, B2>::bytes(ppc);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cs, 1, 1);
+        cfg.blockDim = dim3(kJT, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const int64_t waves = (nmat + nclusters - 1) / nclusters;
+        const int64_t cost = waves * ppc;
+        if (cost <= best_cost) { best_cost = cost; best = cs; }
+    }
+    return best;
+}
+
 template <typename T, int B2>
 cudaError_t launch_jacobi_b2(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
                              int32_t* sweeps, cudaStream_t s) {
     const int b = B2 / 2;
     const int nb = Mp / b;
     const int npairs = nb / 2;
-    const int csize = npairs < kMaxCluster ? npairs : kMaxCluster;
+    const int csize = pick_cluster<T, B2>(nmat, npairs);
     const int ppc = (npairs + csize - 1) / csize;
     const size_t smem = JacobiSmem<T, B2>::bytes(ppc);
     auto kern = k_jacobi<T, B2>;

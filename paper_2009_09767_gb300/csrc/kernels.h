@@ -54,7 +54,7 @@ int jacobi_pad(int M);
 cudaError_t launch_dgemm(int nb, int m, int n, int k, double alpha, const double* A, int64_t lda,
                          int64_t strideA, int tA, const double* B, int64_t ldb, int64_t strideB,
                          int tB, double beta, double* C, int64_t ldc, int64_t strideC,
-                         cudaStream_t s);
+                         cudaStream_t s, int sym = 0);
 // One Ogita-Aishima refinement step for nmat symmetric matrices G with
 // approximate eigenvector rows X (Mp x Mp).  Xn receives the refined rows,
 // lam the eigenvalue estimates.  W1..W3 are Mp x Mp scratch per matrix.
