@@ -3,25 +3,31 @@
 // 2009.09767, Eq. 1: A^i = U^i S^i V^i*, whose U^i and (S^i)^2 are the
 // eigenvectors and eigenvalues of A^i A^i^T).
 //
-// Design (one thread-block cluster per matrix):
-//   * The index set 0..Mp-1 is cut into nb = Mp/b blocks of b = B2/2 indices.
-//     A round-robin (circle) schedule pairs the blocks; each of the nb-1
-//     steps of a sweep handles nb/2 disjoint block pairs in parallel.
-//   * For its pair (I, J) a CTA loads the B2 x B2 sub-matrix G[I+J, I+J] into
-//     shared memory and runs one cyclic Jacobi sweep on it (again a circle
-//     schedule: b disjoint rotations per round, each 2x2 block of the
-//     sub-matrix updated from both sides by one thread), accumulating the
-//     B2 x B2 orthogonal Q.
-//   * Phase A: rows I+J of G and of Vt are replaced by Q^T times themselves
-//     (panel products streamed through shared memory).  Cluster barrier.
-//     Phase B: columns I+J of G by themselves times Q.  Cluster barrier.
+// Design:
+//   * The index set 0..Mp-1 (Mp a multiple of 32) is cut into nb = Mp/16
+//     blocks of 16 indices.  A round-robin (circle) schedule pairs the blocks;
+//     each of the nb-1 steps of a sweep handles nb/2 disjoint block pairs.
+//   * A matrix is owned by a cluster of csize CTAs (512 threads); a CTA owns
+//     ppc = ceil(pairs / csize) pairs per step.  Each pair's 32 x 32
+//     sub-problem G[I+J, I+J] is solved by ONE WARP in shared memory: one
+//     cyclic sweep of 31 rounds x 16 disjoint rotations, synchronised with
+//     __syncwarp only, accumulating the 32 x 32 rotation Q.  Up to 16 pairs
+//     are solved at once by the CTA's 16 warps.
+//   * Phase A: rows I+J of G and of Vt become Q^T times themselves (panel
+//     products through shared memory, all 512 threads).  Cluster barrier.
+//     Phase B: columns I+J of G become themselves times Q.  Cluster barrier.
 //   * A sweep in which no rotation passed the threshold ends the solve.
-// G and Vt stay in global memory (L2-resident at these sizes) and are read
+// G and Vt live in global memory (L2-resident at these sizes) and are read
 // with L2-only loads, because other CTAs of the cluster write them between
-// barriers.  Padding indices (M..Mp-1) hold zero rows/columns: they never
+// barriers.  Padding indices (M..Mp-1) hold zero rows and columns: they never
 // rotate, so their eigenvectors stay exact unit vectors.
+//
+// Two launch forms: k_jacobi (one cluster per matrix, all matrices of one
+// size) and k_jacobi_items (persistent single-CTA workers that take matrices
+// of any size from a work list; used to batch many problems in one launch).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -33,8 +39,13 @@ namespace rk {
 
 namespace {
 
-constexpr int kJT = 512;   // threads per CTA (16 warps)
-constexpr int kMaxCluster = 8;
+constexpr int kJT = 512;          // threads per CTA (16 warps)
+constexpr int kB2 = 32;           // sub-problem size
+constexpr int kB = kB2 / 2;       // index block size
+constexpr int kMaxCluster = 16;
+
+template <typename T> struct PairsMax { static constexpr int value = 16; };
+template <> struct PairsMax<double> { static constexpr int value = 8; };
 
 // circle schedule over n (even) items: partner pair u of round r
 __device__ __forceinline__ void circle_pair(int n, int r, int u, int& a, int& b) {
@@ -58,7 +69,6 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
-// 16-byte vectors of T
 template <typename T> struct V16;
 template <> struct V16<float> {
     using type = float4;
@@ -71,7 +81,6 @@ template <> struct V16<double> {
     __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 };
 
-// Load four consecutive T from 16-byte aligned shared memory.
 template <typename T>
 __device__ __forceinline__ void lds4(const T* p, T (&o)[4]) {
     if constexpr (sizeof(T) == 4) {
@@ -84,39 +93,57 @@ __device__ __forceinline__ void lds4(const T* p, T (&o)[4]) {
     }
 }
 
-template <typename T, int B2>
-struct JacobiSmem {
-    static constexpr int b = B2 / 2;
-    static constexpr int PAD = 16 / (int)sizeof(T);  // keeps rows 16-byte aligned
-    static constexpr int LD = B2 + 1;               // sub-problem stride (odd)
-    static constexpr int QLD = B2 + PAD;            // Q stride (aligned rows)
-    static constexpr int TW = 8192 / B2;            // row-panel tile width
-    static constexpr int RSLD = TW + PAD;           // row-panel stage stride
-    static constexpr int TR = 8192 / B2;            // column-panel tile height
-    static constexpr int CSLD = B2 + 1;             // column-panel stage stride
-    static constexpr int STAGE = (B2 * RSLD > TR * CSLD) ? B2 * RSLD : TR * CSLD;
-    static size_t bytes(int ppc) {
-        return sizeof(T) * ((size_t)B2 * LD + (size_t)ppc * B2 * QLD + (size_t)STAGE) +
-               sizeof(T) * 3 * b + sizeof(int) * 2 * b;
+template <typename T>
+__device__ __forceinline__ void stg4(T* dst, const T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2*>(dst)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(dst)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// Shared-memory layout (in elements of T unless noted):
+//   stage  STAGE             panel tile (16-byte aligned)
+//   Q      ppc x 32 x LD     rotations of this CTA's pairs
+//   sub    ppc x 32 x LD     sub-problems
+//   rot    ppc x 16 x {c, s} rotation table of each warp's current round
+//   pq     ppc x 16 x {p, q} (int)
+template <typename T>
+struct JSmem {
+    static constexpr int LD = kB2 + 1;                 // odd stride: row and column access conflict-free
+    static constexpr int PAD = 16 / (int)sizeof(T);
+    static constexpr int TW = 8192 / kB2;              // row-panel tile width (256)
+    static constexpr int RSLD = TW + PAD;
+    static constexpr int TR = 8192 / kB2;              // column-panel tile height (256)
+    static constexpr int CSLD = kB2 + 1;
+    static constexpr int STAGE = (kB2 * RSLD > TR * CSLD) ? kB2 * RSLD : TR * CSLD;
+    static constexpr size_t bytes(int ppc) {
+        return sizeof(T) * ((size_t)STAGE + 2ull * ppc * kB2 * LD + 2ull * ppc * kB) +
+               sizeof(int) * 2ull * ppc * kB;
     }
 };
 
-// One cyclic sweep (B2-1 rounds) on the shared sub-matrix, accumulating Q.
-// Per round: b threads compute the b disjoint rotations into a table; then
-// every 2x2 block (pair u rows, pair v columns) is updated from both sides by
-// one thread, and the Q columns of each pair by (row, pair) threads.
-template <typename T, int B2>
-__device__ void inner_sweep(T* sub, T* Q, T* cs, T* sn, T* tn, int* pp, int* qq, T tol, T floor_abs,
-                            int* rotated) {
-    using S = JacobiSmem<T, B2>;
-    constexpr int LD = S::LD, QLD = S::QLD, b = S::b;
-    for (int r = 0; r < B2 - 1; ++r) {
-        if (threadIdx.x < b) {
-            const int u = threadIdx.x;
-            int p, q;
-            circle_pair(B2, r, u, p, q);
-            const T a = sub[p * LD + p], d = sub[q * LD + q], g = sub[p * LD + q];
-            T c = T(1), s = T(0), t = T(0);
+// One cyclic sweep of the 32 x 32 sub-problem by one warp, accumulating Q.
+// The 16 rotations of a round are independent, so each lane loads all the
+// values it needs for the 16 of them before updating any: the round's shared
+// memory traffic overlaps instead of forming 16 dependent chains.  A rotation
+// that did not pass the threshold is the identity (c = 1, s = 0).
+template <typename T>
+__device__ void warp_sweep(T* sub, T* Q, T* rc, T* rs, int* rp, int* rq, T tol, T floor_abs,
+                           int& rotated) {
+    constexpr int LD = JSmem<T>::LD;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kB2 - 1; ++r) {
+        T a = T(0), d = T(0), g = T(0), t = T(0);
+        bool rot = false;
+        int p = 0, q = 0;
+        if (lane < kB) {
+            circle_pair(kB2, r, lane, p, q);
+            a = sub[p * LD + p];
+            d = sub[q * LD + q];
+            g = sub[p * LD + q];
+            T c = T(1), s = T(0);
             const T ag = g < T(0) ? -g : g;
             const T rel = tol * sqrt(fabs(a) * fabs(d));
             if (ag > rel && ag > floor_abs) {
@@ -125,89 +152,122 @@ __device__ void inner_sweep(T* sub, T* Q, T* cs, T* sn, T* tn, int* pp, int* qq,
                 t = (zeta >= T(0) ? T(1) : T(-1)) / (az + sqrt(T(1) + zeta * zeta));
                 c = rsqrt_t<T>(T(1) + t * t);
                 s = t * c;
-                *rotated = 1;
+                rot = true;
+                rotated = 1;
             }
-            cs[u] = c; sn[u] = s; tn[u] = t; pp[u] = p; qq[u] = q;
+            rc[lane] = c; rs[lane] = s; rp[lane] = p; rq[lane] = q;
         }
-        __syncthreads();
-        for (int it = threadIdx.x; it < b * b; it += kJT) {
-            const int u = it / b, v = it % b;
-            const int pu = pp[u], qu = qq[u], pv = pp[v], qv = qq[v];
-            const T cu = cs[u], su = sn[u], cv = cs[v], sv = sn[v];
-            if (u == v) {
-                if (su != T(0)) {
-                    const T g = sub[pu * LD + qu];
-                    const T t = tn[u];
-                    sub[pu * LD + pu] = sub[pu * LD + pu] - t * g;
-                    sub[qu * LD + qu] = sub[qu * LD + qu] + t * g;
-                    sub[pu * LD + qu] = T(0);
-                    sub[qu * LD + pu] = T(0);
-                }
-                continue;
+        __syncwarp();
+        // rows p, q of every pair (lane = column), then columns p, q of every
+        // pair and of Q (lane = row); in two halves of 8 pairs to bound the
+        // registers held in flight
+#pragma unroll
+        for (int h = 0; h < kB; h += kB / 2) {
+            T cu[kB / 2], su[kB / 2], x[kB / 2], y[kB / 2];
+            int pu[kB / 2], qu[kB / 2];
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) {
+                cu[u] = rc[h + u]; su[u] = rs[h + u];
+                circle_pair(kB2, r, h + u, pu[u], qu[u]);
             }
-            if (su == T(0) && sv == T(0)) continue;
-            const T x00 = sub[pu * LD + pv], x01 = sub[pu * LD + qv];
-            const T x10 = sub[qu * LD + pv], x11 = sub[qu * LD + qv];
-            const T y00 = cu * x00 - su * x10, y01 = cu * x01 - su * x11;
-            const T y10 = su * x00 + cu * x10, y11 = su * x01 + cu * x11;
-            sub[pu * LD + pv] = cv * y00 - sv * y01;
-            sub[pu * LD + qv] = sv * y00 + cv * y01;
-            sub[qu * LD + pv] = cv * y10 - sv * y11;
-            sub[qu * LD + qv] = sv * y10 + cv * y11;
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) { x[u] = sub[pu[u] * LD + lane]; y[u] = sub[qu[u] * LD + lane]; }
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) {
+                sub[pu[u] * LD + lane] = cu[u] * x[u] - su[u] * y[u];
+                sub[qu[u] * LD + lane] = su[u] * x[u] + cu[u] * y[u];
+            }
         }
-        // Q <- Q R on columns p, q; pair index fastest so a warp touches one row
-        for (int it = threadIdx.x; it < b * B2; it += kJT) {
-            const int u = it % b, row = it / b;
-            const T s = sn[u];
-            if (s == T(0)) continue;
-            const T c = cs[u];
-            const int p = pp[u], q = qq[u];
-            const T x = Q[row * QLD + p], y = Q[row * QLD + q];
-            Q[row * QLD + p] = c * x - s * y;
-            Q[row * QLD + q] = s * x + c * y;
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < kB; h += kB / 2) {
+            T cu[kB / 2], su[kB / 2], x[kB / 2], y[kB / 2];
+            int pu[kB / 2], qu[kB / 2];
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) {
+                cu[u] = rc[h + u]; su[u] = rs[h + u];
+                circle_pair(kB2, r, h + u, pu[u], qu[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) { x[u] = sub[lane * LD + pu[u]]; y[u] = sub[lane * LD + qu[u]]; }
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) {
+                sub[lane * LD + pu[u]] = cu[u] * x[u] - su[u] * y[u];
+                sub[lane * LD + qu[u]] = su[u] * x[u] + cu[u] * y[u];
+            }
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) { x[u] = Q[lane * LD + pu[u]]; y[u] = Q[lane * LD + qu[u]]; }
+#pragma unroll
+            for (int u = 0; u < kB / 2; ++u) {
+                Q[lane * LD + pu[u]] = cu[u] * x[u] - su[u] * y[u];
+                Q[lane * LD + qu[u]] = su[u] * x[u] + cu[u] * y[u];
+            }
         }
-        __syncthreads();
+        __syncwarp();
+        // the rotated 2 x 2 diagonal blocks, exactly
+        if (rot) {
+            sub[p * LD + p] = a - t * g;
+            sub[q * LD + q] = d + t * g;
+            sub[p * LD + q] = T(0);
+            sub[q * LD + p] = T(0);
+        }
+        __syncwarp();
     }
 }
 
-// Global index of local sub-problem index k (0..B2-1) for block pair (bi, bj).
-template <int B2>
 __device__ __forceinline__ int gidx(int bi, int bj, int k) {
-    constexpr int b = B2 / 2;
-    return k < b ? bi * b + k : bj * b + (k - b);
+    return k < kB ? bi * kB + k : bj * kB + (k - kB);
 }
 
-// rows idx(0..B2-1) of Mat (ld = Mp) <- Q^T * rows, over all Mp columns.
-// Tile: B2 rows x TW columns staged in shared memory; each thread computes a
-// 4 x 4 block of outputs with 16-byte shared loads.
-template <typename T, int B2>
+// rows idx(0..31) of Mat (ld = Mp) <- Q^T * rows, over all Mp columns.
+// Tiles of 32 x TW; the global loads of the next tile are issued into
+// registers before the current tile is computed.
+template <typename T>
 __device__ void panel_rows(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage) {
-    using S = JacobiSmem<T, B2>;
-    constexpr int QLD = S::QLD, TW = S::TW, SLD = S::RSLD;
+    using S = JSmem<T>;
+    constexpr int LD = S::LD, TW = S::TW, SLD = S::RSLD;
     constexpr int VN = V16<T>::n;
     using VT = typename V16<T>::type;
-    constexpr int CG = TW / 4;
-    const int ti = threadIdx.x / CG, tc = threadIdx.x % CG;
+    constexpr int PER = kB2 * (TW / VN) / kJT;    // vectors per thread per tile
+    constexpr int CG = TW / 4;                    // 64 column groups
+    const int ti = threadIdx.x / CG, tc = threadIdx.x % CG;   // ti < 8
     const int i0 = ti * 4, j0 = tc * 4;
-    for (int c0 = 0; c0 < Mp; c0 += TW) {
-        const int cw = min(TW, Mp - c0);   // multiple of 32 (Mp is)
-        for (int it = threadIdx.x; it < B2 * (TW / VN); it += kJT) {
+    VT pre[PER];
+    auto load = [&](int c0) {
+        const int cw = min(TW, Mp - c0);
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int it = threadIdx.x + e * kJT;
             const int k = it / (TW / VN), c = (it % (TW / VN)) * VN;
-            VT v;
-            if (c < cw) v = __ldcg(reinterpret_cast<const VT*>(Mat + (int64_t)gidx<B2>(bi, bj, k) * Mp + c0 + c));
-            else v = VT{};
-            *reinterpret_cast<VT*>(stage + k * SLD + c) = v;
+            if (c < cw) pre[e] = __ldcg(reinterpret_cast<const VT*>(Mat + (int64_t)gidx(bi, bj, k) * Mp + c0 + c));
+            else pre[e] = VT{};
         }
-        __syncthreads();
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int it = threadIdx.x + e * kJT;
+            const int k = it / (TW / VN), c = (it % (TW / VN)) * VN;
+            *reinterpret_cast<VT*>(stage + k * SLD + c) = pre[e];
+        }
+    };
+    load(0);
+    stash();
+    __syncthreads();
+    for (int c0 = 0; c0 < Mp; c0 += TW) {
+        const int cw = min(TW, Mp - c0);          // multiple of 32
+        const bool more = c0 + TW < Mp;
+        if (more) load(c0 + TW);
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 #pragma unroll 8
-        for (int k = 0; k < B2; ++k) {
+        for (int k = 0; k < kB2; ++k) {
             T qv[4], xv[4];
-            lds4<T>(Q + k * QLD + i0, qv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qv[i] = Q[k * LD + i0 + i];
             lds4<T>(stage + k * SLD + j0, xv);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -216,55 +276,68 @@ __device__ void panel_rows(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
         }
         if (j0 < cw) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                T* dst = Mat + (int64_t)gidx<B2>(bi, bj, i0 + i) * Mp + c0 + j0;
-                if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-                } else {
-                    reinterpret_cast<double2*>(dst)[0] = make_double2(acc[i][0], acc[i][1]);
-                    reinterpret_cast<double2*>(dst)[1] = make_double2(acc[i][2], acc[i][3]);
-                }
-            }
+            for (int i = 0; i < 4; ++i)
+                stg4<T>(Mat + (int64_t)gidx(bi, bj, i0 + i) * Mp + c0 + j0, acc[i]);
         }
         __syncthreads();
+        if (more) {
+            stash();
+            __syncthreads();
+        }
     }
 }
 
-// columns idx(0..B2-1) of Mat <- columns * Q, over all Mp rows.
-template <typename T, int B2>
+// columns idx(0..31) of Mat <- columns * Q, over all Mp rows; tiles of TR x 32
+// with the next tile's loads in flight during the current one.
+template <typename T>
 __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage) {
-    using S = JacobiSmem<T, B2>;
-    constexpr int QLD = S::QLD, TR = S::TR, SLD = S::CSLD;
+    using S = JSmem<T>;
+    constexpr int LD = S::LD, TR = S::TR, SLD = S::CSLD;
     constexpr int VN = V16<T>::n;
     using VT = typename V16<T>::type;
-    constexpr int JG = B2 / 4;
-    const int tr = threadIdx.x / JG, tj = threadIdx.x % JG;
+    constexpr int PER = TR * (kB2 / VN) / kJT;
+    constexpr int JG = kB2 / 4;                   // 8 column groups
+    const int tr = threadIdx.x / JG, tj = threadIdx.x % JG;   // tr < 64
     const int i0 = tr * 4, j0 = tj * 4;
+    VT pre[PER];
+    auto load = [&](int r0) {
+        const int rh = min(TR, Mp - r0);
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int it = threadIdx.x + e * kJT;
+            const int r = it / (kB2 / VN), k = (it % (kB2 / VN)) * VN;
+            if (r < rh) pre[e] = __ldcg(reinterpret_cast<const VT*>(Mat + (int64_t)(r0 + r) * Mp + gidx(bi, bj, k)));
+            else pre[e] = VT{};
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int it = threadIdx.x + e * kJT;
+            const int r = it / (kB2 / VN), k = (it % (kB2 / VN)) * VN;
+#pragma unroll
+            for (int v = 0; v < VN; ++v) stage[r * SLD + k + v] = V16<T>::get(pre[e], v);
+        }
+    };
+    load(0);
+    stash();
+    __syncthreads();
     for (int r0 = 0; r0 < Mp; r0 += TR) {
         const int rh = min(TR, Mp - r0);
-        for (int it = threadIdx.x; it < TR * (B2 / VN); it += kJT) {
-            const int r = it / (B2 / VN), k = (it % (B2 / VN)) * VN;
-            if (r < rh) {
-                const VT v = __ldcg(reinterpret_cast<const VT*>(Mat + (int64_t)(r0 + r) * Mp + gidx<B2>(bi, bj, k)));
-#pragma unroll
-                for (int e = 0; e < VN; ++e) stage[r * SLD + k + e] = V16<T>::get(v, e);
-            } else {
-#pragma unroll
-                for (int e = 0; e < VN; ++e) stage[r * SLD + k + e] = T(0);
-            }
-        }
-        __syncthreads();
+        const bool more = r0 + TR < Mp;
+        if (more) load(r0 + TR);
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 #pragma unroll 8
-        for (int k = 0; k < B2; ++k) {
+        for (int k = 0; k < kB2; ++k) {
             T xv[4], qv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) xv[i] = stage[(i0 + i) * SLD + k];
-            lds4<T>(Q + k * QLD + j0, qv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) qv[j] = Q[k * LD + j0 + j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -273,47 +346,46 @@ __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (i0 + i >= rh) continue;
-            T* dst = Mat + (int64_t)(r0 + i0 + i) * Mp + gidx<B2>(bi, bj, j0);
-            if constexpr (sizeof(T) == 4) {
-                *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            } else {
-                reinterpret_cast<double2*>(dst)[0] = make_double2(acc[i][0], acc[i][1]);
-                reinterpret_cast<double2*>(dst)[1] = make_double2(acc[i][2], acc[i][3]);
-            }
+            stg4<T>(Mat + (int64_t)(r0 + i0 + i) * Mp + gidx(bi, bj, j0), acc[i]);
         }
         __syncthreads();
+        if (more) {
+            stash();
+            __syncthreads();
+        }
     }
 }
 
-template <typename T, int B2>
-__global__ void __launch_bounds__(kJT, 1)
-k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc, int max_sweeps,
-         T tol, int32_t* __restrict__ sweeps_out) {
-    using SM = JacobiSmem<T, B2>;
-    constexpr int LD = SM::LD, QLD = SM::QLD;
-    constexpr int b = B2 / 2;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int crank = (int)cluster.block_rank();
-    const int mat = blockIdx.x / csize;
-    T* G = Gall + (int64_t)mat * Mp * Mp;
-    T* Vt = Vtall + (int64_t)mat * Mp * Mp;
-    const int nb = Mp / b;
-    const int npairs = nb / 2;
+// Barrier over the CTAs that own one matrix: the cluster, or the CTA alone.
+template <bool kCluster>
+__device__ __forceinline__ void owner_sync() {
+    if constexpr (kCluster) cg::this_cluster().sync();
+    else __syncthreads();
+}
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* stage = reinterpret_cast<T*>(smem_raw);        // 16-byte aligned
-    T* Qs = stage + SM::STAGE;                            // STAGE, QLD keep alignment
-    T* sub = Qs + (size_t)ppc * B2 * QLD;
-    T* cs = sub + (size_t)B2 * LD;
-    T* sn = cs + b;
-    T* tn = sn + b;
-    int* pp = reinterpret_cast<int*>(tn + b);
-    int* qq = pp + b;
+// Solve one matrix.  csize CTAs (rank crank) share it; ppc pairs per CTA.
+template <typename T, bool kCluster>
+__device__ void jacobi_matrix(T* __restrict__ G, T* __restrict__ Vt, int Mp, int csize, int crank,
+                              int ppc, int max_sweeps, T tol, int32_t* __restrict__ sweeps_out,
+                              unsigned char* smem_raw) {
+    using SM = JSmem<T>;
+    constexpr int LD = SM::LD;
+    const int nb = Mp / kB;
+    const int npairs = nb / 2;
+    const int nmine = (npairs - crank + csize - 1) / csize;   // pairs of this CTA per step
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    T* stage = reinterpret_cast<T*>(smem_raw);
+    T* Qs = stage + SM::STAGE;
+    T* subs = Qs + (size_t)ppc * kB2 * LD;
+    T* rcs = subs + (size_t)ppc * kB2 * LD;
+    T* rss = rcs + (size_t)ppc * kB;
+    int* rps = reinterpret_cast<int*>(rss + (size_t)ppc * kB);
+    int* rqs = rps + (size_t)ppc * kB;
     __shared__ int rot_flag;
     __shared__ int decision;
     __shared__ T floor_sh;
 
-    // Vt = I for this CTA's share of rows
     for (int64_t e = (int64_t)crank * kJT + threadIdx.x; e < (int64_t)Mp * Mp;
          e += (int64_t)csize * kJT) {
         const int i = (int)(e / Mp), j = (int)(e % Mp);
@@ -322,80 +394,135 @@ k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc
     // Absolute floor of the rotation threshold: rounding leaves off-diagonal
     // noise of order eps * max|G_ij| <= eps * max_i G_ii in a positive
     // semi-definite matrix, which no rotation can remove.
-    if (threadIdx.x < 32) {
+    if (warp == 0) {
         T dmax = T(0);
-        for (int i = threadIdx.x; i < Mp; i += 32) dmax = fmax(dmax, fabs(ldcg(G + (int64_t)i * Mp + i)));
+        for (int i = lane; i < Mp; i += 32) dmax = fmax(dmax, fabs(ldcg(G + (int64_t)i * Mp + i)));
         for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             floor_sh = T(4) * T(Eps<T>::value) * dmax;
             rot_flag = 0;
         }
     }
-    cluster.sync();
+    owner_sync<kCluster>();
     const T floor_abs = floor_sh;
 
     int sweep = 0;
     bool converged = false;
     while (sweep < max_sweeps) {
+        int rotated = 0;
         for (int step = 0; step < nb - 1; ++step) {
-            // phase A: solve sub-problems, update rows of G and Vt
-            for (int t = 0; t < ppc; ++t) {
-                const int u = crank + t * csize;
-                if (u >= npairs) break;
+            // phase A: warp w solves this CTA's pair w
+            if (warp < nmine) {
+                const int u = crank + warp * csize;
                 int bi, bj;
                 circle_pair(nb, step, u, bi, bj);
-                T* Q = Qs + (size_t)t * B2 * QLD;
-                for (int it = threadIdx.x; it < B2 * B2; it += kJT) {
-                    const int i = it / B2, j = it % B2;
-                    sub[i * LD + j] = ldcg(G + (int64_t)gidx<B2>(bi, bj, i) * Mp + gidx<B2>(bi, bj, j));
-                    Q[i * QLD + j] = i == j ? T(1) : T(0);
+                T* sub = subs + (size_t)warp * kB2 * LD;
+                T* Q = Qs + (size_t)warp * kB2 * LD;
+                for (int i = 0; i < kB2; ++i) {
+                    sub[i * LD + lane] = ldcg(G + (int64_t)gidx(bi, bj, i) * Mp + gidx(bi, bj, lane));
+                    Q[i * LD + lane] = i == lane ? T(1) : T(0);
                 }
-                __syncthreads();
-                inner_sweep<T, B2>(sub, Q, cs, sn, tn, pp, qq, tol, floor_abs, &rot_flag);
-                panel_rows<T, B2>(G, Mp, bi, bj, Q, stage);
-                panel_rows<T, B2>(Vt, Mp, bi, bj, Q, stage);
+                __syncwarp();
+                warp_sweep<T>(sub, Q, rcs + warp * kB, rss + warp * kB, rps + warp * kB,
+                              rqs + warp * kB, tol, floor_abs, rotated);
             }
-            cluster.sync();
-            // phase B: columns of G
-            for (int t = 0; t < ppc; ++t) {
-                const int u = crank + t * csize;
-                if (u >= npairs) break;
+            __syncthreads();
+            for (int t = 0; t < nmine; ++t) {
                 int bi, bj;
-                circle_pair(nb, step, u, bi, bj);
-                panel_cols<T, B2>(G, Mp, bi, bj, Qs + (size_t)t * B2 * QLD, stage);
+                circle_pair(nb, step, crank + t * csize, bi, bj);
+                const T* Q = Qs + (size_t)t * kB2 * LD;
+                panel_rows<T>(G, Mp, bi, bj, Q, stage);
+                panel_rows<T>(Vt, Mp, bi, bj, Q, stage);
             }
-            cluster.sync();
+            owner_sync<kCluster>();
+            // phase B: columns of G
+            for (int t = 0; t < nmine; ++t) {
+                int bi, bj;
+                circle_pair(nb, step, crank + t * csize, bi, bj);
+                panel_cols<T>(G, Mp, bi, bj, Qs + (size_t)t * kB2 * LD, stage);
+            }
+            owner_sync<kCluster>();
         }
         ++sweep;
-        // cluster-wide OR of the rotation flags
-        if (crank == 0 && threadIdx.x == 0) {
-            int any = 0;
-            for (int r = 0; r < csize; ++r) any |= *cluster.map_shared_rank(&rot_flag, r);
-            decision = any;
+        // OR of the rotation flags over the owners
+        if (__syncthreads_or(rotated) && threadIdx.x == 0) rot_flag = 1;
+        __syncthreads();
+        int any;
+        if constexpr (kCluster) {
+            cg::cluster_group cluster = cg::this_cluster();
+            if (crank == 0 && threadIdx.x == 0) {
+                int acc = 0;
+                for (int r = 0; r < csize; ++r) acc |= *cluster.map_shared_rank(&rot_flag, r);
+                decision = acc;
+            }
+            cluster.sync();
+            any = *cluster.map_shared_rank(&decision, 0);
+            cluster.sync();
+        } else {
+            any = rot_flag;
+            __syncthreads();
         }
-        cluster.sync();
-        const int any = *cluster.map_shared_rank(&decision, 0);
-        cluster.sync();
         if (threadIdx.x == 0) rot_flag = 0;
         __syncthreads();
         if (!any) { converged = true; break; }
     }
-    if (crank == 0 && threadIdx.x == 0) sweeps_out[mat] = converged ? sweep : -sweep;
+    if (crank == 0 && threadIdx.x == 0) *sweeps_out = converged ? sweep : -sweep;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kJT, 1)
+k_jacobi(T* __restrict__ Gall, T* __restrict__ Vtall, int Mp, int csize, int ppc, int max_sweeps,
+         T tol, int32_t* __restrict__ sweeps_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int crank = (int)cg::this_cluster().block_rank();
+    const int mat = blockIdx.x / csize;
+    jacobi_matrix<T, true>(Gall + (int64_t)mat * Mp * Mp, Vtall + (int64_t)mat * Mp * Mp, Mp, csize,
+                           crank, ppc, max_sweeps, tol, sweeps_out + mat, smem_raw);
+}
+
+// Persistent workers: each CTA takes the next matrix of the list until none is left.
+template <typename T>
+__global__ void __launch_bounds__(kJT, 1)
+k_jacobi_items(const JacobiItem* __restrict__ items, int nitems, int* __restrict__ next,
+               int max_sweeps, T tol) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int item_sh;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = item_sh;
+        __syncthreads();
+        if (it >= nitems) break;
+        const JacobiItem w = items[it];
+        const int ppc = w.Mp / kB2;
+        jacobi_matrix<T, false>(static_cast<T*>(w.G), static_cast<T*>(w.Vt), w.Mp, 1, 0, ppc,
+                                max_sweeps, tol, w.sweeps, smem_raw);
+        __syncthreads();
+    }
 }
 
 // Cluster size for nmat matrices with npairs block pairs per step.  A CTA
-// handles ppc = ceil(npairs / csize) pairs per step, so a matrix takes time
-// ~ ppc; clusters run in waves of the hardware's maximum active clusters for
-// that size.  Choose the size with the fewest waves * ppc (ties: the larger
-// cluster, lower latency per matrix).
-template <typename T, int B2>
+// owns ppc = ceil(npairs / csize) pairs; its step costs about one warp sweep
+// (the pairs' warps run in parallel) plus ppc pairs of panel products, so a
+// matrix takes ~ (kInner + ppc).  Clusters run in waves of the hardware's
+// maximum active clusters of that size.  Minimise waves * (kInner + ppc);
+// ties go to the larger cluster (lower latency per matrix).
+constexpr int kInner = 2;
+
+template <typename T>
 int pick_cluster(int nmat, int npairs) {
-    auto kern = k_jacobi<T, B2>;
-    int best = 1;
+    auto kern = k_jacobi<T>;
+    int best = -1;
     int64_t best_cost = INT64_MAX;
     for (int cs = 1; cs <= kMaxCluster && cs <= npairs; cs *= 2) {
         const int ppc = (npairs + cs - 1) / cs;
-        const size_t smem = JacobiSmem<T, B2>::bytes(ppc);
+        if (ppc > PairsMax<T>::value) continue;
+        const size_t smem = JSmem<T>::bytes(ppc);
+        if (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                          cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess) {
             cudaGetLastError();
@@ -418,22 +545,31 @@ int pick_cluster(int nmat, int npairs) {
             continue;
         }
         const int64_t waves = (nmat + nclusters - 1) / nclusters;
-        const int64_t cost = waves * ppc;
+        const int64_t cost = waves * (kInner + ppc);
         if (cost <= best_cost) { best_cost = cost; best = cs; }
     }
     return best;
 }
 
-template <typename T, int B2>
-cudaError_t launch_jacobi_b2(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
-                             int32_t* sweeps, cudaStream_t s) {
-    const int b = B2 / 2;
-    const int nb = Mp / b;
-    const int npairs = nb / 2;
-    const int csize = pick_cluster<T, B2>(nmat, npairs);
+}  // namespace
+
+int jacobi_pad(int M) { return (int)round_up(M, kB2); }
+
+int jacobi_item_max_mp(bool fp64) { return kB2 * (fp64 ? PairsMax<double>::value : PairsMax<float>::value); }
+
+template <typename T>
+cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
+                          int32_t* sweeps, cudaStream_t s) {
+    if (nmat <= 0) return cudaSuccess;
+    if (Mp % kB2 != 0) return cudaErrorInvalidValue;
+    const int npairs = Mp / kB2;
+    const int csize = pick_cluster<T>(nmat, npairs);
+    if (csize < 1) return cudaErrorInvalidConfiguration;
     const int ppc = (npairs + csize - 1) / csize;
-    const size_t smem = JacobiSmem<T, B2>::bytes(ppc);
-    auto kern = k_jacobi<T, B2>;
+    const size_t smem = JSmem<T>::bytes(ppc);
+    auto kern = k_jacobi<T>;
+    if (csize > 8)
+        RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nmat * csize), 1, 1);
@@ -450,21 +586,32 @@ cudaError_t launch_jacobi_b2(T* G, T* Vt, int nmat, int Mp, int max_sweeps, doub
     return cudaLaunchKernelEx(&cfg, kern, G, Vt, Mp, csize, ppc, max_sweeps, (T)tol, sweeps);
 }
 
-}  // namespace
-
-int jacobi_pad(int M) { return M <= 32 ? 32 : (int)round_up(M, 64); }
-
 template <typename T>
-cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
-                          int32_t* sweeps, cudaStream_t s) {
-    if (nmat <= 0) return cudaSuccess;
-    if (Mp == 32) return launch_jacobi_b2<T, 32>(G, Vt, nmat, Mp, max_sweeps, tol, sweeps, s);
-    return launch_jacobi_b2<T, 64>(G, Vt, nmat, Mp, max_sweeps, tol, sweeps, s);
+cudaError_t launch_jacobi_items(const JacobiItem* items, int nitems, int max_mp, int* next,
+                                int max_sweeps, double tol, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    const int ppc = max_mp / kB2;
+    if (max_mp % kB2 != 0 || ppc < 1 || ppc > PairsMax<T>::value) return cudaErrorInvalidValue;
+    const size_t smem = JSmem<T>::bytes(ppc);
+    auto kern = k_jacobi_items<T>;
+    RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    RK_CUDA_TRY(cudaGetDevice(&dev));
+    RK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJT, smem));
+    const int grid = std::max(1, std::min(nitems, sms * std::max(per_sm, 1)));
+    RK_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
+    k_jacobi_items<T><<<grid, kJT, smem, s>>>(items, nitems, next, max_sweeps, (T)tol);
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_jacobi<float>(float*, float*, int, int, int, double, int32_t*,
                                           cudaStream_t);
 template cudaError_t launch_jacobi<double>(double*, double*, int, int, int, double, int32_t*,
                                            cudaStream_t);
+template cudaError_t launch_jacobi_items<float>(const JacobiItem*, int, int, int*, int, double,
+                                                cudaStream_t);
+template cudaError_t launch_jacobi_items<double>(const JacobiItem*, int, int, int*, int, double,
+                                                 cudaStream_t);
 
 }  // namespace rk

@@ -46,8 +46,25 @@ cudaError_t launch_convert_f32_f64(const float* src, double* dst, int64_t n, cud
 template <typename T>
 cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
                           int32_t* sweeps, cudaStream_t s);
-// Sub-problem size used for an Mp x Mp matrix (Mp must be a multiple of it).
+// Padded order of an M x M problem (a multiple of 32).
 int jacobi_pad(int M);
+
+// One matrix of a persistent batched solve: G and Vt (Mp x Mp, element type of
+// the launch), the sweep counter it reports to.
+struct JacobiItem {
+    void* G;
+    void* Vt;
+    int32_t* sweeps;
+    int32_t Mp;
+    int32_t pad;
+};
+// Largest Mp one persistent worker CTA can hold.
+int jacobi_item_max_mp(bool fp64);
+// Persistent workers over nitems matrices of order <= max_mp (items in device
+// memory; next is a device int used as the work counter).
+template <typename T>
+cudaError_t launch_jacobi_items(const JacobiItem* items, int nitems, int max_mp, int* next,
+                                int max_sweeps, double tol, cudaStream_t s);
 
 // ---- dense.cu: FP64 batched products, refinement, sort/rank, proxy, merge ----
 // C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, op = transpose if t*.
