@@ -186,6 +186,222 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (one JSON line each, rank 0 only; not the headline metric)
+
+def _plain_one_at_a_time(cases, device, n=24):
+    """The plain FP64 GPU method: one svd_run per matrix, synchronised, no
+    batching or graphs.  Returns (matrices/s, per-matrix latencies in ms)."""
+    import torch
+
+    import paper_2009_09767_gb300 as rk
+    lat = []
+    t_all = 0.0
+    for c in cases[:n]:
+        p = rk.Plan(c.M, c.N, c.nnz, max(1, c.num_blocks), value_type="f32", precision="fp64")
+        o = rk.alloc_outputs(p, device=device, with_patches=False)
+        cp, ri, va = (torch.from_numpy(c.col_ptr).to(device), torch.from_numpy(c.row_idx).to(device),
+                      torch.from_numpy(c.vals).to(device))
+        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"])
+        p.sync()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"])
+        p.sync()
+        dt = time.perf_counter() - t0
+        lat.append(dt * 1e3)
+        t_all += dt
+        p.free()
+    return len(lat) / t_all, lat
+
+
+def run_batch(args):
+    """Batched workload: independent matrices, M ~ U{32..256}, N ~ logU[1e3, 2e5],
+    density ~ logU[0.5%, 5%], N(0,1) values; block width from the autotuner;
+    one batched pass (graph-replayed) per step."""
+    import torch
+
+    import paper_2009_09767_gb300 as rk
+    import synth
+    from paper_2009_09767_gb300 import autotune
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    cases = synth.batch_mix(args.count)
+    t_gen = time.perf_counter() - t0
+    print(f"# generated {len(cases)} matrices in {t_gen:.1f} s", file=sys.stderr, flush=True)
+    width, rates = autotune.tune(cases, args.precision, sample=min(64, len(cases)))
+    print(f"# autotuned width {width}: {rates}", file=sys.stderr, flush=True)
+    for c in cases:
+        c.num_blocks = autotune.blocks_for(c.N, width)
+    plans, inputs, outs = [], [], []
+    for c in cases:
+        p = rk.Plan(c.M, c.N, c.nnz, c.num_blocks, value_type="f32", precision=args.precision)
+        plans.append(p)
+        inputs.append((torch.from_numpy(c.col_ptr).to(dev), torch.from_numpy(c.row_idx).to(dev),
+                       torch.from_numpy(c.vals).to(dev)))
+        outs.append(rk.alloc_outputs(p, device=dev, with_patches=False))
+    batch = rk.Batch(plans, graph=True)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(1, args.warmup)):
+        batch.run(inputs, outs, stream=stream)
+    batch.sync()
+    torch.cuda.synchronize(dev)
+    launches = batch.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batch.run(inputs, outs, stream=stream)
+    ev1.record(stream)
+    batch.sync()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    value = len(cases) / (ms / 1e3)
+    plain_rate, plain_lat = _plain_one_at_a_time(cases, dev)
+    v_entries = sum(c.N * c.M for c in cases)
+    line = {
+        "metric": "matrices/s (batched, " + args.precision + ")", "value": value, "unit": "SVD/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"batch_mix x{len(cases)} M 32-256 N 1e3-2e5 density 0.5-5%",
+                   "precision": args.precision, "block_width": width,
+                   "nnz_total": int(sum(c.nnz for c in cases)), "V_entries": int(v_entries),
+                   "graph": True},
+        "autotune": rates, "gpu_launches_per_pass": launches,
+        "plain_fp64_one_at_a_time": {"value": plain_rate, "unit": "SVD/s",
+                                     "p50_ms": float(np.percentile(plain_lat, 50)),
+                                     "p99_ms": float(np.percentile(plain_lat, 99)),
+                                     "sample": f"first {len(plain_lat)} matrices, svd_run + sync each"},
+        "speedup_vs_plain": value / plain_rate,
+        "V_write_gbs": v_entries * (4 if args.precision == "mixed" else 8) / (ms / 1e3) / 1e9,
+        "generate_s": t_gen,
+    }
+    print(json.dumps(line), flush=True)
+    batch.free()
+    for p in plans:
+        p.free()
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals of batch_mix-shaped requests with 5%
+    zipf_wide-shaped ones, 40 GB device budget; p50/p99 latency (arrival to
+    results on the host) and completed requests/s, per arrival rate."""
+    import torch
+
+    import paper_2009_09767_gb300 as rk
+    import synth
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(synth.SEED_BASE + 5)
+    templates = synth.batch_mix(256, seed=synth.SEED_BASE + 5)
+    for c in templates:
+        c.num_blocks = 1
+    wide = synth.zipf_wide()
+    out = {"metric": "serving p50/p99 latency and throughput", "unit": "ms", "data": "synthetic",
+           "config": {"workload": "Poisson arrivals, 95% batch_mix-shaped, 5% zipf_wide-shaped "
+                                  "(512 x 1e6), V copied back", "budget_bytes": 40 << 30,
+                      "max_inflight": 16, "duration_s_per_rate": args.duration},
+           "rates": []}
+    pinned = {}
+
+    def outputs_for(c, prec, slot):
+        key = (c.M, c.N, prec, slot)
+        if key not in pinned:
+            pinned[key] = rk.host_outputs(c.M, c.N, min(c.M, c.N), prec, pinned=True)
+        return pinned[key]
+
+    for prec in ("mixed", "fp64"):
+        for rate in [float(r) for r in args.rates.split(",")]:
+            srv = rk.Server(40 << 30, max_inflight=16)
+            n = max(1, int(rate * args.duration))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            kinds = rng.random(n) < 0.05
+            picks = rng.integers(0, len(templates), size=n)
+            tickets = []
+            t_start = time.perf_counter()
+            wide_slot = 0
+            for i in range(n):
+                delay = t_start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                if kinds[i]:
+                    c, slot = wide, wide_slot % 3
+                    wide_slot += 1
+                else:
+                    c, slot = templates[picks[i]], i % 4
+                o = outputs_for(c, prec, slot)
+                tickets.append(srv.submit(c.M, c.N, c.col_ptr, c.row_idx, c.vals, c.num_blocks, o,
+                                          precision=prec))
+            lat, fails, last_done = [], 0, 0.0
+            first = None
+            for t in tickets:
+                st = srv.wait(t, timeout=600.0)
+                ts, ta, td = srv.times(t)
+                first = ts if first is None else min(first, ts)
+                last_done = max(last_done, td)
+                if st != 0:
+                    fails += 1
+                else:
+                    lat.append((td - ts) * 1e3)
+                srv.release(t)
+            stats = srv.stats()
+            srv.close()
+            out["rates"].append({
+                "precision": prec, "rate_req_s": rate, "requests": n, "failed": fails,
+                "completed_per_s": len(lat) / max(last_done - first, 1e-9),
+                "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+                "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+                "pool_peak_gb": stats["pool_peak"] / 2**30})
+    print(json.dumps(out), flush=True)
+
+
+def run_single_case(args):
+    """One large (1024 x 8e6, ~80M nnz, 256 lognormal blocks, k=100) or small
+    (64 x 4096, 4 blocks) SVD, timed like the headline."""
+    import torch
+
+    import paper_2009_09767_gb300 as rk
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.workload == "large":
+        c = synth.large_skewed(N=args.large_cols, D=max(1, int(round(256 * args.large_cols / 8e6))))
+        bounds = np.concatenate([[0], np.cumsum(c.widths)]).astype(np.int64)
+        k = 100
+    else:
+        c = synth.small_uniform().with_values(np.float32)
+        bounds, k = None, 0
+    p = rk.Plan(c.M, c.N, c.nnz, c.num_blocks, value_type="f32", precision=args.precision,
+                bounds=bounds, k=k, flags=rk.FLAG_TIMING)
+    o = rk.alloc_outputs(p, device=dev, with_patches=False)
+    cp, ri, va = (torch.from_numpy(c.col_ptr).to(dev), torch.from_numpy(c.row_idx).to(dev),
+                  torch.from_numpy(c.vals).to(dev))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(1, args.warmup)):
+        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"], stream=stream)
+    p.sync()
+    p.query(rk.Q_STAGE_TOTAL)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"], stream=stream)
+    ev1.record(stream)
+    p.sync()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    totals = p.query(rk.Q_STAGE_TOTAL)
+    line = {"metric": "SVD/s (" + args.workload + ", " + args.precision + ")",
+            "value": 1e3 / ms, "unit": "SVD/s", "ms_per_step": ms, "steps": args.steps,
+            "config": {"workload": f"{c.name} M={c.M} N={c.N} nnz={c.nnz} D={c.num_blocks} "
+                                   f"k={p.k}", "precision": args.precision},
+            "stage_ms": {n: float(totals[i] / max(totals[-1], 1)) for i, n in enumerate(rk.STAGES)},
+            "sweeps": p.query(rk.Q_SWEEPS).tolist()[-1], "rank": int(o["rank"].item()),
+            "sigma_head": o["sigma"][:3].cpu().tolist()}
+    print(json.dumps(line), flush=True)
+    p.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,10 +414,22 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cols", type=int, default=1_000_000,
                     help="columns of the zipf_wide matrix (smaller cases for profiling)")
+    ap.add_argument("--workload", default="zipf_wide",
+                    choices=["zipf_wide", "batch", "serve", "large", "small"],
+                    help="zipf_wide (default, the headline), batch (many matrices in one "
+                         "pass), serve (Poisson arrivals), large (1024 x 8e6), small (64 x 4096)")
+    ap.add_argument("--count", type=int, default=2000, help="batch: matrices")
+    ap.add_argument("--rates", default="50,100,200,400", help="serve: arrival rates (req/s)")
+    ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds per rate")
+    ap.add_argument("--large-cols", type=int, default=8_000_000, help="large: columns")
     args = ap.parse_args()
 
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "zipf_wide":
+        {"batch": run_batch, "serve": run_serve, "large": run_single_case,
+         "small": run_single_case}[args.workload](args)
         return
 
     import torch

@@ -119,6 +119,11 @@ typedef struct svd_plan_s* svd_plan_t;
  * SVD_ERR_OOM without allocating anything on failure. */
 svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* device_bytes_needed);
 
+/* Like svd_plan, on caller-provided device workspace (256-byte aligned, at
+ * least svd_plan_bytes); svd_free does not free it. */
+svd_status svd_plan_ws(const svd_desc* desc, void* d_workspace, size_t workspace_bytes,
+                       svd_plan_t* out);
+
 /* Workspace size for desc without allocating (for admission control). */
 svd_status svd_plan_bytes(const svd_desc* desc, size_t* device_bytes_needed);
 
@@ -178,6 +183,87 @@ enum {
                                 count; resets the sums */
 };
 svd_status svd_query(svd_plan_t plan, int32_t what, int64_t index, void* h_dst, size_t bytes);
+
+/* ---- Batches: many plans in one pass (all plans' block eigensolves in one
+ * persistent launch, likewise the merge eigensolves; the per-matrix stages on
+ * a pool of worker streams).  Each plan keeps its own workspace; the batch
+ * object adds the work lists, streams and (optionally) a CUDA graph. */
+typedef struct {
+    const int64_t* d_col_ptr;
+    const int32_t* d_row_idx;
+    const void* d_vals;
+    double* d_sigma;
+    double* d_U;
+    void* d_V;
+    int32_t* d_rank;
+    svd_patch* d_patches;   /* may be NULL (with d_npatches) */
+    int64_t* d_npatches;
+} svd_io;
+
+typedef struct svd_batch_s* svd_batch_t;
+
+#define SVD_BATCH_GRAPH 1   /* capture the pass into a CUDA graph on the first run and replay
+                               it on later runs that pass the same svd_io buffers (a different
+                               set of buffers is captured anew) */
+
+/* Group n plans (which must stay alive until svd_batch_free; each plan in at
+ * most one batch that runs at a time). */
+svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, svd_batch_t* out);
+/* Enqueue one SVD per plan, ios[i] for plans[i] (same conventions as
+ * svd_run), on `stream`; asynchronous. */
+svd_status svd_batch_run(svd_batch_t batch, const svd_io* ios, void* stream);
+/* Wait for the batch and return the worst device-detected status. */
+svd_status svd_batch_sync(svd_batch_t batch);
+/* Kernels launched by the last non-replayed run (0 if none). */
+int64_t svd_batch_launches(svd_batch_t batch);
+void svd_batch_free(svd_batch_t batch);
+
+/* ---- Serving: a continuous-batching SVD service on one GPU.  A scheduler
+ * thread admits submitted requests in arrival order as stream slots and room
+ * in the device-memory budget free up; each admitted request gets its plan
+ * workspace, CSC and outputs from one pool allocation inside the budget and
+ * runs on its slot's stream (host->device copies, svd_run, device->host
+ * copies), overlapping with the requests already running. */
+typedef struct svd_server_s* svd_server_t;
+
+typedef struct {
+    svd_desc desc;             /* block_col_bounds (if any) is copied at submit */
+    const int64_t* h_col_ptr;  /* host CSC; must stay valid until the request is done */
+    const int32_t* h_row_idx;
+    const void* h_vals;
+    double* h_sigma;           /* host outputs (as svd_run_host); pinned memory is faster */
+    double* h_U;
+    void* h_V;                 /* may be NULL: V is not copied back */
+    int32_t* h_rank;
+} svd_request;
+
+/* budget_bytes: device memory the service may use (allocated once);
+ * max_inflight: requests on the GPU at the same time (one stream each). */
+svd_status svd_server_create(size_t budget_bytes, int32_t max_inflight, svd_server_t* out);
+/* Queue a request; SVD_ERR_BUDGET when it can never fit in the budget. */
+svd_status svd_server_submit(svd_server_t srv, const svd_request* req, uint64_t* ticket);
+/* *done = 1 once finished; *result = the request's status (SVD_OK on success). */
+svd_status svd_server_poll(svd_server_t srv, uint64_t ticket, int32_t* done, svd_status* result);
+/* Block until the request finishes or timeout_s passes (SVD_ERR_TIMEOUT). */
+svd_status svd_server_wait(svd_server_t srv, uint64_t ticket, double timeout_s, svd_status* result);
+/* Drop a request that has not been admitted yet (its result becomes
+ * SVD_ERR_INVALID_ARG); running requests cannot be cancelled. */
+svd_status svd_server_cancel(svd_server_t srv, uint64_t ticket);
+/* Submit, admission and completion times (seconds, steady clock). */
+svd_status svd_server_times(svd_server_t srv, uint64_t ticket, double* t_submit,
+                            double* t_admit, double* t_done);
+/* Forget a finished ticket. */
+svd_status svd_server_release(svd_server_t srv, uint64_t ticket);
+/* out[8]: submitted, completed, failed, rejected, running, queued, pool bytes
+ * in use, peak pool bytes. */
+svd_status svd_server_stats(svd_server_t srv, int64_t* out);
+/* Host-side fault injection for tests: make the request with `ticket`
+ * (submitted later) fail its pool allocation, or carry a malformed CSC. */
+#define SVD_INJECT_ALLOC 1
+#define SVD_INJECT_BAD_CSC 2
+svd_status svd_server_inject(svd_server_t srv, int32_t what, uint64_t ticket);
+/* Drops queued requests, waits for running ones, frees everything. */
+void svd_server_destroy(svd_server_t srv);
 
 /* Right singular vectors without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate device memory on

@@ -310,3 +310,190 @@ def right_vectors_static(M, N, col_ptr, row_idx, vals, sigma, U, V, *, k=None, r
            _ptr(sigma), _ptr(U), float(rank_tol), _ptr(patches), _ptr(npatches), int(max_patches),
            vv, _ptr(V), _stream_handle(stream))
     _check(st, "svd_right_vectors_static")
+
+
+class SvdIo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("col_ptr", "row_idx", "vals", "sigma", "U", "V",
+                                                "rank", "patches", "npatches")]
+
+
+BATCH_GRAPH = 1
+
+
+class Batch:
+    """svd_batch_*: many plans in one pass (see include/ranky.h)."""
+
+    def __init__(self, plans, graph: bool = False):
+        lib = load_library()
+        for name, args, res in (
+            ("svd_batch_create", [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+            ("svd_batch_run", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+            ("svd_batch_sync", [ctypes.c_void_p], ctypes.c_int32),
+            ("svd_batch_launches", [ctypes.c_void_p], ctypes.c_int64),
+            ("svd_batch_free", [ctypes.c_void_p], None),
+        ):
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.svd_batch_create(len(self.plans), arr, BATCH_GRAPH if graph else 0,
+                                    ctypes.byref(h)), "svd_batch_create")
+        self._h = h
+        self._ios = None
+
+    def run(self, inputs, outputs, stream=None):
+        """inputs[i] = (col_ptr, row_idx, vals); outputs[i] = alloc_outputs(plan i)."""
+        lib = load_library()
+        ios = (SvdIo * len(self.plans))()
+        for i, ((cp, ri, va), o) in enumerate(zip(inputs, outputs)):
+            ios[i] = SvdIo(cp.data_ptr(), ri.data_ptr() if ri.numel() else None,
+                           va.data_ptr() if va.numel() else None, o["sigma"].data_ptr(),
+                           o["U"].data_ptr(), o["V"].data_ptr(), o["rank"].data_ptr(),
+                           o["patches"].data_ptr() if "patches" in o else None,
+                           o["npatches"].data_ptr() if "npatches" in o else None)
+        self._ios = ios
+        _check(lib.svd_batch_run(self._h, ctypes.byref(ios), _stream_handle(stream)),
+               "svd_batch_run")
+
+    def sync(self):
+        _check(load_library().svd_batch_sync(self._h), "svd_batch_sync")
+
+    def launches(self) -> int:
+        return int(load_library().svd_batch_launches(self._h))
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load_library().svd_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class SvdRequest(ctypes.Structure):
+    _fields_ = [("desc", SvdDesc), ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("U", ctypes.c_void_p),
+                ("V", ctypes.c_void_p), ("rank", ctypes.c_void_p)]
+
+
+INJECT_ALLOC = 1
+INJECT_BAD_CSC = 2
+
+
+class Server:
+    """svd_server_*: continuous-batching service (see include/ranky.h).  Host
+    arrays passed to submit() are kept alive here until release()."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 8):
+        lib = load_library()
+        P, I32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+        for name, args, res in (
+            ("svd_server_create", [ctypes.c_size_t, I32, ctypes.POINTER(P)], I32),
+            ("svd_server_submit", [P, ctypes.POINTER(SvdRequest), ctypes.POINTER(U64)], I32),
+            ("svd_server_poll", [P, U64, ctypes.POINTER(I32), ctypes.POINTER(I32)], I32),
+            ("svd_server_wait", [P, U64, ctypes.c_double, ctypes.POINTER(I32)], I32),
+            ("svd_server_cancel", [P, U64], I32),
+            ("svd_server_times", [P, U64, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], I32),
+            ("svd_server_release", [P, U64], I32),
+            ("svd_server_stats", [P, P], I32),
+            ("svd_server_inject", [P, I32, U64], I32),
+            ("svd_server_destroy", [P], None),
+        ):
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        h = ctypes.c_void_p()
+        _check(lib.svd_server_create(int(budget_bytes), int(max_inflight), ctypes.byref(h)),
+               "svd_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, M, N, col_ptr, row_idx, vals, num_blocks, outputs, **kw) -> int:
+        """Host arrays in (numpy or pinned torch CPU tensors); outputs = dict with
+        host 'sigma', 'U' (k x M), 'V' (N x k, or None) and 'rank'."""
+        vt = "f32" if vals.dtype in (np.float32,) or str(vals.dtype).endswith("float32") else "f64"
+        d, keep = make_desc(M, N, len(row_idx), num_blocks, value_type=vt, **kw)
+        req = SvdRequest(d, _ptr(col_ptr), _ptr(row_idx) if len(row_idx) else None,
+                         _ptr(vals) if len(vals) else None, _ptr(outputs["sigma"]),
+                         _ptr(outputs["U"]), _ptr(outputs.get("V")), _ptr(outputs["rank"]))
+        t = ctypes.c_uint64(0)
+        _check(load_library().svd_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
+               "svd_server_submit")
+        self._keep[t.value] = (col_ptr, row_idx, vals, outputs, keep)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout: float = 60.0) -> int:
+        """Returns the request's status (0 = ok); raises on timeout."""
+        res = ctypes.c_int32(0)
+        _check(load_library().svd_server_wait(self._h, ticket, float(timeout), ctypes.byref(res)),
+               "svd_server_wait")
+        return int(res.value)
+
+    def wait_status(self, ticket: int, timeout: float):
+        """(call status, request status) without raising."""
+        res = ctypes.c_int32(-1)
+        st = load_library().svd_server_wait(self._h, ticket, float(timeout), ctypes.byref(res))
+        return int(st), int(res.value)
+
+    def poll(self, ticket: int):
+        done, res = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load_library().svd_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(res)),
+               "svd_server_poll")
+        return bool(done.value), int(res.value)
+
+    def cancel(self, ticket: int) -> int:
+        return int(load_library().svd_server_cancel(self._h, ticket))
+
+    def times(self, ticket: int):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load_library().svd_server_times(self._h, ticket, ctypes.byref(a), ctypes.byref(b),
+                                               ctypes.byref(c)), "svd_server_times")
+        return a.value, b.value, c.value
+
+    def release(self, ticket: int):
+        _check(load_library().svd_server_release(self._h, ticket), "svd_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        out = np.zeros(8, np.int64)
+        _check(load_library().svd_server_stats(self._h, _ptr(out)), "svd_server_stats")
+        keys = ["submitted", "completed", "failed", "rejected", "running", "queued", "pool_used",
+                "pool_peak"]
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def inject(self, what: int, ticket: int):
+        _check(load_library().svd_server_inject(self._h, int(what), int(ticket)), "svd_server_inject")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().svd_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def host_outputs(M, N, k, precision="mixed", with_v=True, pinned=False):
+    """Host output buffers for Server.submit / Plan.run_host."""
+    vdt = np.float32 if precision == "mixed" else np.float64
+    out = {"sigma": np.zeros(k), "U": np.zeros((k, M)), "rank": np.zeros(1, np.int32),
+           "V": np.zeros((N, k), vdt) if with_v else None}
+    if pinned:
+        import torch
+        for key in ("sigma", "U", "rank", "V"):
+            if out[key] is not None:
+                t = torch.from_numpy(out[key]).pin_memory()
+                out[key] = t.numpy()
+                out[key + "_pinned"] = t
+    return out

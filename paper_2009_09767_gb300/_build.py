@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libranky.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
 SOURCES = ["partition.cu", "gram.cu", "jacobi.cu", "dense.cu", "spmm.cu", "api.cu",
-           "static_scratch.cu"]
+           "static_scratch.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, s):
             jobs.append([cc, *ARCH, *FLAGS, *(extra or []), "-c", s, "-o", o])
@@ -55,7 +55,8 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if force or jobs or not os.path.exists(OUT):
         tmp = OUT + f".tmp{os.getpid()}"
-        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"],
+                           capture_output=True, text=True)
         if r.returncode != 0:
             print(r.stdout, r.stderr)
             raise RuntimeError("link failed")

@@ -33,7 +33,7 @@ struct svd_plan_s {
     int64_t N = 0, nnz = 0;
     bool mixed = false, random = false;
     double jac_tol = 0.0;
-    int max_sweeps = 40, refine_iters = 1, merge_refine_iters = 2;
+    int max_sweeps = 40, refine_iters = 1, merge_refine_iters = 3;
     std::vector<int64_t> bounds_h;
     int nchunks = 0;
     int W = 0;  // bitmap words per block
@@ -42,6 +42,7 @@ struct svd_plan_s {
 
     char* arena = nullptr;
     size_t arena_bytes = 0;
+    bool owns_arena = true;
 
     int64_t* bounds_d = nullptr;
     int32_t* chunk_block = nullptr;
@@ -103,6 +104,7 @@ struct svd_plan_s {
     double stage_total[kStages] = {};
     int64_t stage_runs = 0;
     bool timing = false;
+    int cur_slot = -1;
 };
 
 namespace {
@@ -245,6 +247,7 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
         cudaError_t _e = (expr);                               \
         if (_e != cudaSuccess) {                               \
             fprintf(stderr, "ranky: %s: %s\n", #expr, cudaGetErrorString(_e)); \
+            cudaGetLastError();                                \
             return SVD_ERR_CUDA;                               \
         }                                                      \
         (plan)->launches += (n);                               \
@@ -255,19 +258,39 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
         cudaError_t _e = (expr);                                \
         if (_e != cudaSuccess) {                                \
             fprintf(stderr, "ranky: %s: %s\n", #expr, cudaGetErrorString(_e)); \
+            cudaGetLastError();                                 \
             return SVD_ERR_CUDA;                                \
         }                                                       \
     } while (0)
 
-svd_status run_device(svd_plan_s* p, const int64_t* col_ptr, const int32_t* row_idx,
-                      const void* vals, double* d_sigma, double* d_U, void* d_V, int32_t* d_rank,
-                      svd_patch* d_patches, int64_t* d_npatches, cudaStream_t s) {
-    const int D = p->D, M = p->M, Mp = p->Mp;
-    const int64_t mm = (int64_t)Mp * Mp;
-    const int vt = p->d.value_type;
-    p->launches = 0;
+struct RunIO {
+    const int64_t* col_ptr;
+    const int32_t* row_idx;
+    const void* vals;
+    double* sigma;
+    double* U;
+    void* V;
+    int32_t* rank;
+    svd_patch* patches;
+    int64_t* npatches;
+};
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Stage-time events of one run (SVD_FLAG_TIMING; not while a stream is
+// being captured into a graph).
+void timing_begin(svd_plan_s* p, cudaStream_t s) {
+    p->cur_slot = -1;
+    if (!p->timing || capturing(s)) return;
     const int slot = (int)(p->run_index % kRing);
-    if (p->timing && p->ev_pending[slot]) {
+    if (p->ev_pending[slot]) {
         // the run that used this slot kRing runs ago: fold its times into the totals
         cudaEventSynchronize(p->ev[slot][kStages]);
         for (int i = 0; i < kStages; ++i) {
@@ -278,84 +301,118 @@ svd_status run_device(svd_plan_s* p, const int64_t* col_ptr, const int32_t* row_
         ++p->stage_runs;
         p->ev_pending[slot] = false;
     }
-    auto mark = [&](int i) {
-        if (p->timing) cudaEventRecord(p->ev[slot][i], s);
-    };
-    mark(0);
+    p->cur_slot = slot;
+}
 
+void mark(svd_plan_s* p, int i, cudaStream_t s) {
+    if (p->cur_slot >= 0) cudaEventRecord(p->ev[p->cur_slot][i], s);
+}
+
+// Up to the block eigensolve: Algorithm 1 scan, Algorithm 2 insertions, Eq. 2
+// cross products; leaves the matrices the block Jacobi works on.
+svd_status phase_pre(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
+    const int D = p->D, M = p->M, Mp = p->Mp;
+    const int64_t mm = (int64_t)Mp * Mp;
+    const int vt = p->d.value_type;
+    p->launches = 0;
+    timing_begin(p, s);
+    mark(p, 0, s);
     CU(cudaMemsetAsync(p->occ, 0, sizeof(uint32_t) * (size_t)D * p->W, s));
     CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
-    // Algorithm 1: per-block row occupancy, lonely nodes; Algorithm 2 patches
-    LAUNCH(p, 1, launch_occupancy(col_ptr, row_idx, vals, vt, M, p->nchunks, p->chunk_block,
-                                  p->chunk_lo, p->chunk_hi, p->occ, s));
+    LAUNCH(p, 1, launch_occupancy(io.col_ptr, io.row_idx, io.vals, vt, M, p->nchunks,
+                                  p->chunk_block, p->chunk_lo, p->chunk_hi, p->occ, s));
     LAUNCH(p, 1, launch_lonely_patches(p->occ, D, M, p->bounds_d, p->random ? 1 : 0, p->d.seed,
                                        p->row_ne, p->lonely, p->patches, p->patch_ofs,
-                                       reinterpret_cast<PatchRec*>(d_patches), d_npatches, s));
-    mark(1);
-    // Eq. 2: block cross products
-    LAUNCH(p, 1, launch_gram(col_ptr, row_idx, vals, vt, Mp, p->nchunks, p->chunk_block,
+                                       reinterpret_cast<PatchRec*>(io.patches), io.npatches, s));
+    mark(p, 1, s);
+    LAUNCH(p, 1, launch_gram(io.col_ptr, io.row_idx, io.vals, vt, Mp, p->nchunks, p->chunk_block,
                              p->chunk_lo, p->chunk_hi, p->G64, s));
     if (p->random)
-        LAUNCH(p, 1, launch_gram_patches(col_ptr, row_idx, vals, vt, Mp, D, p->patches,
+        LAUNCH(p, 1, launch_gram_patches(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->patches,
                                          p->patch_ofs, D * M, p->G64, s));
     LAUNCH(p, 1, launch_symmetrize(p->G64, D, Mp, s));
+    mark(p, 2, s);
+    if (!p->mixed)
+        CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * D * mm, cudaMemcpyDeviceToDevice, s));
+    else
+        LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, (int64_t)D * mm, s));
+    return SVD_OK;
+}
 
-    mark(2);
-    // Eq. 1: block eigensolves
+svd_status block_jacobi(svd_plan_s* p, cudaStream_t s) {
+    if (!p->mixed)
+        LAUNCH(p, 1, launch_jacobi<double>(p->Gw64, p->Vt64, p->D, p->Mp, p->max_sweeps,
+                                           p->jac_tol, p->sweeps, s));
+    else
+        LAUNCH(p, 1, launch_jacobi<float>(p->G32, p->Vt32, p->D, p->Mp, p->max_sweeps, p->jac_tol,
+                                          p->sweeps, s));
+    return SVD_OK;
+}
+
+// Block refinement, sort and rank, proxy P and P P^T (Eqs. 2-3); leaves the
+// merge matrix for the merge eigensolve.
+svd_status phase_mid(svd_plan_s* p, cudaStream_t s) {
+    const int D = p->D, M = p->M, Mp = p->Mp;
+    const int64_t mm = (int64_t)Mp * Mp;
+    mark(p, 3, s);
     const double* Xblk64 = nullptr;
     const float* Xblk32 = nullptr;
     if (!p->mixed) {
-        CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * D * mm, cudaMemcpyDeviceToDevice, s));
-        LAUNCH(p, 1, launch_jacobi<double>(p->Gw64, p->Vt64, D, Mp, p->max_sweeps, p->jac_tol,
-                                           p->sweeps, s));
         LAUNCH(p, 1, launch_sort_rank(nullptr, nullptr, p->Gw64, nullptr, D, M, Mp, p->bounds_d, 0,
                                       p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
-        mark(3);
         Xblk64 = p->Vt64;
-    } else {
-        LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, (int64_t)D * mm, s));
-        LAUNCH(p, 1, launch_jacobi<float>(p->G32, p->Vt32, D, Mp, p->max_sweeps, p->jac_tol,
-                                          p->sweeps, s));
-        mark(3);
-        if (p->refine_iters > 0) {
-            LAUNCH(p, 1, launch_convert_f32_f64(p->Vt32, p->Vt64, (int64_t)D * mm, s));
-            double* X = p->Vt64;
-            double* Xn = p->Xn;
-            for (int it = 0; it < p->refine_iters; ++it) {
-                LAUNCH(p, 7, launch_refine(p->G64, X, Xn, p->lam, D, Mp, p->RW1, p->RW2, p->RW3,
-                                           p->norms, s));
-                std::swap(X, Xn);
-            }
-            LAUNCH(p, 1, launch_sort_rank(p->lam, nullptr, nullptr, nullptr, D, M, Mp, p->bounds_d,
-                                          0, p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
-            Xblk64 = X;
-        } else {
-            LAUNCH(p, 1, launch_sort_rank(nullptr, nullptr, nullptr, p->G32, D, M, Mp, p->bounds_d,
-                                          0, p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
-            Xblk32 = p->Vt32;
+    } else if (p->refine_iters > 0) {
+        LAUNCH(p, 1, launch_convert_f32_f64(p->Vt32, p->Vt64, (int64_t)D * mm, s));
+        double* X = p->Vt64;
+        double* Xn = p->Xn;
+        for (int it = 0; it < p->refine_iters; ++it) {
+            LAUNCH(p, 7, launch_refine(p->G64, X, Xn, p->lam, D, Mp, p->RW1, p->RW2, p->RW3,
+                                       p->norms, s));
+            std::swap(X, Xn);
         }
+        LAUNCH(p, 1, launch_sort_rank(p->lam, nullptr, nullptr, nullptr, D, M, Mp, p->bounds_d, 0,
+                                      p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
+        Xblk64 = X;
+    } else {
+        LAUNCH(p, 1, launch_sort_rank(nullptr, nullptr, nullptr, p->G32, D, M, Mp, p->bounds_d, 0,
+                                      p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
+        Xblk32 = p->Vt32;
     }
-    mark(4);
-    // proxy P = [U^1 S^1 | ... | U^D S^D] and P P^T (Eqs. 2-3)
+    mark(p, 4, s);
     LAUNCH(p, 2, launch_proxy(Xblk64, Xblk32, p->bsig, p->bperm, p->brank, D, M, Mp, p->pofs, p->P,
                               s));
-    mark(5);
+    mark(p, 5, s);
     LAUNCH(p, 2, launch_merge_gram(p->P, p->pofs, D, M, Mp, p->Rmax, p->partial, p->nsplit,
                                    p->S64, s));
-    mark(6);
-    // merge eigensolve
+    mark(p, 6, s);
+    if (!p->mixed)
+        CU(cudaMemcpyAsync(p->Sw64, p->S64, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
+    else
+        LAUNCH(p, 1, launch_convert_f64_f32(p->S64, p->S32, mm, s));
+    return SVD_OK;
+}
+
+svd_status merge_jacobi(svd_plan_s* p, cudaStream_t s) {
+    if (!p->mixed)
+        LAUNCH(p, 1, launch_jacobi<double>(p->Sw64, p->SV64, 1, p->Mp, p->max_sweeps, p->jac_tol,
+                                           p->sweeps + p->D, s));
+    else
+        LAUNCH(p, 1, launch_jacobi<float>(p->S32, p->SV32, 1, p->Mp, p->max_sweeps, p->jac_tol,
+                                          p->sweeps + p->D, s));
+    return SVD_OK;
+}
+
+// Merge refinement, sigma / U / rank / W, and V = A'^T W.
+svd_status phase_post(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
+    const int D = p->D, M = p->M, Mp = p->Mp;
+    const int64_t mm = (int64_t)Mp * Mp;
+    const int vt = p->d.value_type;
     const double* Xm64 = nullptr;
     if (!p->mixed) {
-        CU(cudaMemcpyAsync(p->Sw64, p->S64, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
-        LAUNCH(p, 1, launch_jacobi<double>(p->Sw64, p->SV64, 1, Mp, p->max_sweeps, p->jac_tol,
-                                           p->sweeps + D, s));
         LAUNCH(p, 1, launch_sort_rank(nullptr, nullptr, p->Sw64, nullptr, 1, M, Mp, nullptr, p->N,
                                       p->d.rank_tol, p->msig, p->mperm, p->mrank, s));
         Xm64 = p->SV64;
     } else {
-        LAUNCH(p, 1, launch_convert_f64_f32(p->S64, p->S32, mm, s));
-        LAUNCH(p, 1, launch_jacobi<float>(p->S32, p->SV32, 1, Mp, p->max_sweeps, p->jac_tol,
-                                          p->sweeps + D, s));
         LAUNCH(p, 1, launch_convert_f32_f64(p->SV32, p->SV64, mm, s));
         double* X = p->SV64;
         double* Xn = p->SXn;
@@ -368,34 +425,45 @@ svd_status run_device(svd_plan_s* p, const int64_t* col_ptr, const int32_t* row_
                                       p->d.rank_tol, p->msig, p->mperm, p->mrank, s));
         Xm64 = X;
     }
-    mark(7);
+    mark(p, 7, s);
     const double lam_abs = p->d.rank_tol > 0 ? p->d.rank_tol * p->d.rank_tol : 0.0;
     const int64_t tol_scale = std::max<int64_t>(M, p->N);
     LAUNCH(p, 1, launch_finalize(Xm64, nullptr, p->msig, p->mperm, M, Mp, p->k, lam_abs, tol_scale,
-                                 d_sigma, d_U, d_rank, p->W64, p->W32, s));
-    mark(8);
-    // V = A'^T W
-    if (!(p->d.flags & SVD_FLAG_SKIP_V) && d_V) {
+                                 io.sigma, io.U, io.rank, p->W64, p->W32, s));
+    mark(p, 8, s);
+    if (!(p->d.flags & SVD_FLAG_SKIP_V) && io.V) {
         if (p->mixed) {
-            LAUNCH(p, 1, launch_spmm<float>(col_ptr, row_idx, vals, vt, p->N, p->k, p->W32,
-                                            static_cast<float*>(d_V), s));
+            LAUNCH(p, 1, launch_spmm<float>(io.col_ptr, io.row_idx, io.vals, vt, p->N, p->k, p->W32,
+                                            static_cast<float*>(io.V), s));
             if (p->random)
                 LAUNCH(p, 1, launch_spmm_patches<float>(p->patches, p->patch_ofs + D, D * M, p->k,
-                                                        p->W32, static_cast<float*>(d_V), s));
+                                                        p->W32, static_cast<float*>(io.V), s));
         } else {
-            LAUNCH(p, 1, launch_spmm<double>(col_ptr, row_idx, vals, vt, p->N, p->k, p->W64,
-                                             static_cast<double*>(d_V), s));
+            LAUNCH(p, 1, launch_spmm<double>(io.col_ptr, io.row_idx, io.vals, vt, p->N, p->k,
+                                             p->W64, static_cast<double*>(io.V), s));
             if (p->random)
                 LAUNCH(p, 1, launch_spmm_patches<double>(p->patches, p->patch_ofs + D, D * M, p->k,
-                                                         p->W64, static_cast<double*>(d_V), s));
+                                                         p->W64, static_cast<double*>(io.V), s));
         }
     }
-    mark(9);
-    if (p->timing) p->ev_pending[slot] = true;
+    mark(p, 9, s);
+    if (p->cur_slot >= 0) p->ev_pending[p->cur_slot] = true;
     ++p->run_index;
     p->last_stream = s;
     p->ran = true;
     return SVD_OK;
+}
+
+svd_status run_device(svd_plan_s* p, const int64_t* col_ptr, const int32_t* row_idx,
+                      const void* vals, double* d_sigma, double* d_U, void* d_V, int32_t* d_rank,
+                      svd_patch* d_patches, int64_t* d_npatches, cudaStream_t s) {
+    const RunIO io{col_ptr, row_idx, vals, d_sigma, d_U, d_V, d_rank, d_patches, d_npatches};
+    svd_status st = phase_pre(p, io, s);
+    if (st == SVD_OK) st = block_jacobi(p, s);
+    if (st == SVD_OK) st = phase_mid(p, s);
+    if (st == SVD_OK) st = merge_jacobi(p, s);
+    if (st == SVD_OK) st = phase_post(p, io, s);
+    return st;
 }
 
 }  // namespace
@@ -431,7 +499,10 @@ svd_status svd_plan_bytes(const svd_desc* desc, size_t* bytes) {
     return SVD_OK;
 }
 
-svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* bytes) {
+namespace {
+// Create a plan on `arena` (nullptr: allocate one).
+svd_status plan_create(const svd_desc* desc, void* arena, size_t arena_bytes, svd_plan_t* out,
+                       size_t* bytes) {
     if (!out) return SVD_ERR_INVALID_ARG;
     *out = nullptr;
     svd_status st = validate_desc(desc);
@@ -443,7 +514,14 @@ svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* bytes) {
     Carver dry{nullptr, 0, true};
     carve(p, dry);
     p->arena_bytes = dry.off;
-    if (cudaMalloc(&p->arena, p->arena_bytes) != cudaSuccess) {
+    if (arena) {
+        if (arena_bytes < p->arena_bytes || (reinterpret_cast<uintptr_t>(arena) & 255u)) {
+            delete p;
+            return SVD_ERR_INVALID_ARG;
+        }
+        p->arena = static_cast<char*>(arena);
+        p->owns_arena = false;
+    } else if (cudaMalloc(&p->arena, p->arena_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return SVD_ERR_OOM;
@@ -471,7 +549,7 @@ svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* bytes) {
                           cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemset(p->sweeps, 0, sizeof(int32_t) * (p->D + 1)) == cudaSuccess;
     if (!ok) {
-        cudaFree(p->arena);
+        if (p->owns_arena) cudaFree(p->arena);
         delete p;
         return SVD_ERR_CUDA;
     }
@@ -483,6 +561,17 @@ svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* bytes) {
     if (bytes) *bytes = p->arena_bytes;
     *out = p;
     return SVD_OK;
+}
+}  // namespace
+
+svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* bytes) {
+    return plan_create(desc, nullptr, 0, out, bytes);
+}
+
+svd_status svd_plan_ws(const svd_desc* desc, void* d_workspace, size_t workspace_bytes,
+                       svd_plan_t* out) {
+    if (!d_workspace) return SVD_ERR_INVALID_ARG;
+    return plan_create(desc, d_workspace, workspace_bytes, out, nullptr);
 }
 
 svd_status svd_run(svd_plan_t p, const int64_t* d_col_ptr, const int32_t* d_row_idx,
@@ -567,7 +656,7 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
 svd_status svd_sync(svd_plan_t p) {
     if (!p) return SVD_ERR_INVALID_ARG;
     if (!p->ran) return SVD_OK;
-    CU(cudaStreamSynchronize(p->last_stream));
+    if (p->last_stream) CU(cudaStreamSynchronize(p->last_stream));
     std::vector<int32_t> sw(p->D + 1);
     CU(cudaMemcpy(sw.data(), p->sweeps, sizeof(int32_t) * (p->D + 1), cudaMemcpyDeviceToHost));
     for (int32_t v : sw)
@@ -687,12 +776,284 @@ svd_status svd_query(svd_plan_t p, int32_t what, int64_t index, void* h_dst, siz
 void svd_free(svd_plan_t p) {
     if (!p) return;
     if (p->last_stream) cudaStreamSynchronize(p->last_stream);
-    if (p->arena) cudaFree(p->arena);
+    if (p->arena && p->owns_arena) cudaFree(p->arena);
     if (p->host_arena) cudaFree(p->host_arena);
     if (p->timing)
         for (int r = 0; r < kRing; ++r)
             for (int i = 0; i <= kStages; ++i) cudaEventDestroy(p->ev[r][i]);
     delete p;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many plans in one pass.  The per-matrix stages of the plans run
+// on a pool of worker streams; all block eigensolves of all plans go to one
+// persistent Jacobi launch fed from a work list (matrices of any order up to
+// the worker's capacity), and the merge eigensolves to another.  Optionally
+// the whole pass is captured into a CUDA graph on the first run and replayed.
+
+struct svd_batch_s {
+    std::vector<svd_plan_s*> plans;
+    std::vector<cudaStream_t> streams;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join_ev;
+    // work lists: [blocks f32 | blocks f64 | merges f32 | merges f64]
+    JacobiItem* d_items = nullptr;
+    int* d_next = nullptr;
+    int count[4] = {};
+    int offset[4] = {};
+    int maxmp[4] = {};
+    double tol[4] = {};
+    int sweeps_cap = 40;
+    std::vector<int> outsized;   // plans whose Mp exceeds the worker capacity
+    bool use_graph = false;
+    bool captured = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // graphs are captured and replayed here
+    cudaEvent_t in_ev = nullptr, out_ev = nullptr;
+    std::vector<RunIO> ios_seen;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void fork(svd_batch_s* b, cudaStream_t s) {
+    cudaEventRecord(b->fork_ev, s);
+    for (cudaStream_t w : b->streams) cudaStreamWaitEvent(w, b->fork_ev, 0);
+}
+
+void join(svd_batch_s* b, cudaStream_t s) {
+    for (size_t i = 0; i < b->streams.size(); ++i) {
+        cudaEventRecord(b->join_ev[i], b->streams[i]);
+        cudaStreamWaitEvent(s, b->join_ev[i], 0);
+    }
+}
+
+svd_status batch_items(svd_batch_s* b, int first, cudaStream_t s) {
+    // first = 0: block work lists, 2: merge work lists
+    for (int w = first; w < first + 2; ++w) {
+        if (!b->count[w]) continue;
+        cudaError_t e = (w % 2 == 0)
+            ? launch_jacobi_items<float>(b->d_items + b->offset[w], b->count[w], b->maxmp[w],
+                                         b->d_next + w, b->sweeps_cap, b->tol[w], s)
+            : launch_jacobi_items<double>(b->d_items + b->offset[w], b->count[w], b->maxmp[w],
+                                          b->d_next + w, b->sweeps_cap, b->tol[w], s);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "ranky: batched Jacobi: %s\n", cudaGetErrorString(e));
+            return SVD_ERR_CUDA;
+        }
+        ++b->launches;
+    }
+    return SVD_OK;
+}
+
+svd_status batch_enqueue(svd_batch_s* b, const RunIO* ios, cudaStream_t s) {
+    const size_t n = b->plans.size(), ns = b->streams.size();
+    b->launches = 0;
+    svd_status st = SVD_OK;
+    fork(b, s);
+    for (size_t i = 0; i < n && st == SVD_OK; ++i)
+        st = phase_pre(b->plans[i], ios[i], b->streams[i % ns]);
+    join(b, s);
+    if (st != SVD_OK) return st;
+    if ((st = batch_items(b, 0, s)) != SVD_OK) return st;
+    for (int i : b->outsized)
+        if ((st = block_jacobi(b->plans[i], s)) != SVD_OK) return st;
+    fork(b, s);
+    for (size_t i = 0; i < n && st == SVD_OK; ++i) st = phase_mid(b->plans[i], b->streams[i % ns]);
+    join(b, s);
+    if (st != SVD_OK) return st;
+    if ((st = batch_items(b, 2, s)) != SVD_OK) return st;
+    for (int i : b->outsized)
+        if ((st = merge_jacobi(b->plans[i], s)) != SVD_OK) return st;
+    fork(b, s);
+    for (size_t i = 0; i < n && st == SVD_OK; ++i)
+        st = phase_post(b->plans[i], ios[i], b->streams[i % ns]);
+    join(b, s);
+    for (size_t i = 0; i < n; ++i) b->launches += b->plans[i]->launches;
+    return st;
+}
+
+bool same_ios(const std::vector<RunIO>& a, const RunIO* b, size_t n) {
+    if (a.size() != n) return false;
+    return memcmp(a.data(), b, sizeof(RunIO) * n) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, svd_batch_t* out) {
+    if (!out || n < 1 || !plans) return SVD_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!plans[i]) return SVD_ERR_INVALID_ARG;
+    svd_batch_s* b = new (std::nothrow) svd_batch_s();
+    if (!b) return SVD_ERR_OOM;
+    b->plans.assign(plans, plans + n);
+    b->use_graph = (flags & SVD_BATCH_GRAPH) != 0;
+    const int ns = std::min(n, 8);
+    bool ok = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->in_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->out_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    b->streams.resize(ns);
+    b->join_ev.resize(ns);
+    for (int i = 0; i < ns && ok; ++i) {
+        ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    // work lists
+    std::vector<JacobiItem> lists[4];
+    const int cap32 = jacobi_item_max_mp(false), cap64 = jacobi_item_max_mp(true);
+    for (int i = 0; i < n; ++i) {
+        svd_plan_s* p = plans[i];
+        const bool f64 = !p->mixed;
+        if (p->Mp > (f64 ? cap64 : cap32)) {
+            b->outsized.push_back(i);
+            continue;
+        }
+        const int64_t mm = (int64_t)p->Mp * p->Mp;
+        const int wb = f64 ? 1 : 0;
+        for (int d = 0; d < p->D; ++d) {
+            JacobiItem it{};
+            it.G = f64 ? (void*)(p->Gw64 + d * mm) : (void*)(p->G32 + d * mm);
+            it.Vt = f64 ? (void*)(p->Vt64 + d * mm) : (void*)(p->Vt32 + d * mm);
+            it.sweeps = p->sweeps + d;
+            it.Mp = p->Mp;
+            lists[wb].push_back(it);
+        }
+        JacobiItem m{};
+        m.G = f64 ? (void*)p->Sw64 : (void*)p->S32;
+        m.Vt = f64 ? (void*)p->SV64 : (void*)p->SV32;
+        m.sweeps = p->sweeps + p->D;
+        m.Mp = p->Mp;
+        lists[2 + wb].push_back(m);
+        for (int w : {wb, 2 + wb}) {
+            b->maxmp[w] = std::max(b->maxmp[w], p->Mp);
+            b->tol[w] = p->jac_tol;
+        }
+        b->sweeps_cap = std::max(b->sweeps_cap, p->max_sweeps);
+    }
+    size_t total = 0;
+    for (int w = 0; w < 4; ++w) {
+        b->offset[w] = (int)total;
+        b->count[w] = (int)lists[w].size();
+        total += lists[w].size();
+    }
+    if (ok && total) {
+        ok = cudaMalloc(&b->d_items, sizeof(JacobiItem) * total) == cudaSuccess &&
+             cudaMalloc(&b->d_next, sizeof(int) * 4) == cudaSuccess;
+        for (int w = 0; w < 4 && ok; ++w)
+            if (b->count[w])
+                ok = cudaMemcpy(b->d_items + b->offset[w], lists[w].data(),
+                                sizeof(JacobiItem) * b->count[w], cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        svd_batch_free(b);
+        return SVD_ERR_OOM;
+    }
+    *out = b;
+    return SVD_OK;
+}
+
+svd_status svd_batch_run(svd_batch_t b, const svd_io* ios, void* stream) {
+    if (!b || !ios) return SVD_ERR_INVALID_ARG;
+    const size_t n = b->plans.size();
+    std::vector<RunIO> rio(n);
+    for (size_t i = 0; i < n; ++i) {
+        const svd_io& o = ios[i];
+        svd_plan_s* p = b->plans[i];
+        if (!o.d_col_ptr || (p->nnz > 0 && (!o.d_row_idx || !o.d_vals)) || !o.d_sigma || !o.d_U ||
+            !o.d_rank || (!o.d_V && !(p->d.flags & SVD_FLAG_SKIP_V)) ||
+            ((o.d_patches == nullptr) != (o.d_npatches == nullptr)))
+            return SVD_ERR_INVALID_ARG;
+        rio[i] = RunIO{o.d_col_ptr, o.d_row_idx, o.d_vals, o.d_sigma, o.d_U, o.d_V, o.d_rank,
+                       o.d_patches, o.d_npatches};
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!b->use_graph) return batch_enqueue(b, rio.data(), s);
+    // The graph is captured on, and replayed on, the batch's own stream, which
+    // is ordered after the caller's stream (event in) and before it (event out):
+    // the caller's stream may be the legacy default stream, which cannot be
+    // captured.
+    cudaStream_t cs = b->cap_stream;
+    CU(cudaEventRecord(b->in_ev, s));
+    CU(cudaStreamWaitEvent(cs, b->in_ev, 0));
+    if (!(b->captured && same_ios(b->ios_seen, rio.data(), n))) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+            b->captured = false;
+        }
+        CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        svd_status st = batch_enqueue(b, rio.data(), cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+        if (st != SVD_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (ce != cudaSuccess) fprintf(stderr, "ranky: batch capture: %s\n", cudaGetErrorString(ce));
+            return st != SVD_OK ? st : SVD_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            fprintf(stderr, "ranky: batch graph: %s\n", cudaGetErrorString(ie));
+            cudaGetLastError();
+            b->exec = nullptr;
+            return SVD_ERR_CUDA;
+        }
+        b->captured = true;
+        b->ios_seen = rio;
+    }
+    CU(cudaGraphLaunch(b->exec, cs));
+    CU(cudaEventRecord(b->out_ev, cs));
+    CU(cudaStreamWaitEvent(s, b->out_ev, 0));
+    for (svd_plan_s* p : b->plans) { p->last_stream = cs; p->ran = true; }
+    return SVD_OK;
+}
+
+svd_status svd_batch_sync(svd_batch_t b) {
+    if (!b) return SVD_ERR_INVALID_ARG;
+    for (cudaStream_t w : b->streams) CU(cudaStreamSynchronize(w));
+    if (b->cap_stream) CU(cudaStreamSynchronize(b->cap_stream));
+    svd_status worst = SVD_OK;
+    for (svd_plan_s* p : b->plans) {
+        const svd_status st = svd_sync(p);
+        if (st != SVD_OK) worst = st;
+    }
+    return worst;
+}
+
+int64_t svd_batch_launches(svd_batch_t b) { return b ? b->launches : 0; }
+
+void svd_batch_free(svd_batch_t b) {
+    if (!b) return;
+    for (cudaStream_t w : b->streams)
+        if (w) cudaStreamSynchronize(w);
+    if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
+    // the plans outlive the batch: they must not keep its streams
+    for (svd_plan_s* p : b->plans)
+        for (cudaStream_t w : b->streams)
+            if (p->last_stream == w || p->last_stream == b->cap_stream) p->last_stream = nullptr;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t w : b->streams)
+        if (w) cudaStreamDestroy(w);
+    for (cudaEvent_t e : b->join_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->cap_stream) {
+        cudaStreamSynchronize(b->cap_stream);
+        cudaStreamDestroy(b->cap_stream);
+    }
+    if (b->in_ev) cudaEventDestroy(b->in_ev);
+    if (b->out_ev) cudaEventDestroy(b->out_ev);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_next) cudaFree(b->d_next);
+    delete b;
 }
 
 }  // extern "C"

@@ -1,0 +1,479 @@
+// server.cpp -- continuous-batching SVD service on one GPU (include/ranky.h,
+// svd_server_*).
+//
+// A scheduler thread owns the device: it admits submitted requests in arrival
+// order whenever a stream slot is free and the request fits in what is left
+// of the device-memory budget, places its plan workspace, CSC and outputs in
+// one allocation from a first-fit pool over a single budget-sized device
+// buffer, and enqueues host->device copies, svd_run and device->host copies
+// on the slot's stream.  Requests that arrive while others are running are
+// admitted as slots and memory free up, so their kernels overlap on the GPU.
+// Completion is detected by polling a CUDA event per request; the request's
+// pool memory and plan are released at once and its latency stamped.
+//
+// Fault injection for the tests is host-side only: a chosen ticket can be
+// made to fail its pool allocation (SVD_INJECT_ALLOC) or to have its CSC
+// treated as malformed (SVD_INJECT_BAD_CSC).  Nothing here makes the GPU
+// fault or wait forever.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ranky.h"
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// First-fit allocator over [0, size) with 256-byte granules.
+class Pool {
+public:
+    explicit Pool(size_t size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = align256(std::max<size_t>(bytes, 1));
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align256(std::max<size_t>(bytes, 1));
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+    size_t peak() const { return peak_; }
+
+private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0, peak_ = 0;
+};
+
+enum State { kPending = 0, kRunning = 1, kDone = 2 };
+
+struct Request {
+    uint64_t ticket = 0;
+    svd_desc desc{};
+    std::vector<int64_t> bounds;
+    svd_request io{};
+    State state = kPending;
+    svd_status result = SVD_OK;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t plan_bytes = 0, total_bytes = 0, off = 0;
+    svd_plan_t plan = nullptr;
+    int slot = -1;
+    cudaEvent_t done_ev = nullptr;
+    bool inject_alloc = false, inject_bad_csc = false;
+};
+
+struct Layout {
+    size_t plan, col_ptr, row_idx, vals, sigma, U, V, rank, total;
+};
+
+Layout layout(const svd_desc& d, size_t plan_bytes) {
+    const int64_t k = d.k > 0 ? d.k : std::min<int64_t>(d.M, d.N);
+    const size_t sv = d.value_type == SVD_VALUE_F32 ? 4 : 8;
+    const size_t sV = d.precision == SVD_PREC_MIXED ? 4 : 8;
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t at = off; off += align256(std::max<size_t>(bytes, 1)); return at; };
+    L.plan = take(plan_bytes);
+    L.col_ptr = take(sizeof(int64_t) * (size_t)(d.N + 1));
+    L.row_idx = take(sizeof(int32_t) * (size_t)d.nnz);
+    L.vals = take(sv * (size_t)d.nnz);
+    L.sigma = take(sizeof(double) * (size_t)k);
+    L.U = take(sizeof(double) * (size_t)d.M * (size_t)k);
+    L.V = take((d.flags & SVD_FLAG_SKIP_V) ? 1 : sV * (size_t)d.N * (size_t)k);
+    L.rank = take(sizeof(int32_t));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct svd_server_s {
+    int device = 0;
+    size_t budget = 0;
+    char* base = nullptr;
+    Pool* pool = nullptr;
+    int max_inflight = 1;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> slot_busy;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> pending;
+    std::vector<Request*> running;
+    std::unordered_map<uint64_t, Request*> all;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_rejected = 0;
+    std::unordered_map<uint64_t, int> injections;
+};
+
+namespace {
+
+void finish(svd_server_s* s, Request* r, svd_status st) {
+    r->result = st;
+    r->state = kDone;
+    r->t_done = now_s();
+    if (st == SVD_OK) ++s->n_completed; else ++s->n_failed;
+}
+
+// Start one admitted request on its slot (scheduler thread, lock NOT held:
+// the copies from pageable host memory can block this thread).  Returns the
+// status; SVD_OK means the work is enqueued and r->done_ev recorded.
+svd_status start(svd_server_s* s, Request* r) {
+    cudaStream_t st = s->streams[r->slot];
+    char* at = s->base + r->off;
+    const Layout L = layout(r->desc, r->plan_bytes);
+    svd_status res = svd_plan_ws(&r->desc, at + L.plan, r->plan_bytes, &r->plan);
+    if (res != SVD_OK) return res;
+    const svd_desc& d = r->desc;
+    const int64_t k = d.k > 0 ? d.k : std::min<int64_t>(d.M, d.N);
+    const size_t sv = d.value_type == SVD_VALUE_F32 ? 4 : 8;
+    const size_t sV = d.precision == SVD_PREC_MIXED ? 4 : 8;
+    const bool want_v = r->io.h_V && !(d.flags & SVD_FLAG_SKIP_V);
+    auto* cp = reinterpret_cast<int64_t*>(at + L.col_ptr);
+    auto* ri = reinterpret_cast<int32_t*>(at + L.row_idx);
+    void* va = at + L.vals;
+    auto* sg = reinterpret_cast<double*>(at + L.sigma);
+    auto* U = reinterpret_cast<double*>(at + L.U);
+    void* V = at + L.V;
+    auto* rk = reinterpret_cast<int32_t*>(at + L.rank);
+    bool ok = cudaMemcpyAsync(cp, r->io.h_col_ptr, sizeof(int64_t) * (d.N + 1),
+                              cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (d.nnz > 0) {
+        ok = ok && cudaMemcpyAsync(ri, r->io.h_row_idx, sizeof(int32_t) * d.nnz,
+                                   cudaMemcpyHostToDevice, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(va, r->io.h_vals, sv * d.nnz, cudaMemcpyHostToDevice, st) ==
+                       cudaSuccess;
+    }
+    if (!ok) { cudaGetLastError(); return SVD_ERR_CUDA; }
+    if (r->inject_bad_csc) {
+        // the host-side stand-in for a malformed request: a column pointer
+        // that does not end at nnz, which the CSC check rejects
+        int64_t bad = d.nnz + 1;
+        cudaMemcpyAsync(cp + d.N, &bad, sizeof(bad), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    if (d.flags & SVD_FLAG_CHECK_CSC) {
+        res = svd_check_csc(d.M, d.N, d.nnz, cp, ri, st);
+        if (res != SVD_OK) return res;
+    }
+    res = svd_run(r->plan, cp, ri, va, sg, U, want_v ? V : nullptr, rk, nullptr, nullptr, st);
+    if (res != SVD_OK) return res;
+    ok = cudaMemcpyAsync(r->io.h_sigma, sg, sizeof(double) * k, cudaMemcpyDeviceToHost, st) ==
+         cudaSuccess;
+    ok = ok && cudaMemcpyAsync(r->io.h_U, U, sizeof(double) * d.M * k, cudaMemcpyDeviceToHost,
+                               st) == cudaSuccess;
+    if (want_v)
+        ok = ok && cudaMemcpyAsync(r->io.h_V, V, sV * (size_t)d.N * k, cudaMemcpyDeviceToHost,
+                                   st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(r->io.h_rank, rk, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ==
+                   cudaSuccess;
+    ok = ok && cudaEventRecord(r->done_ev, st) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return SVD_ERR_CUDA; }
+    return SVD_OK;
+}
+
+void release(svd_server_s* s, Request* r) {
+    if (r->plan) { svd_free(r->plan); r->plan = nullptr; }
+    if (r->total_bytes) { s->pool->release(r->off, r->total_bytes); r->total_bytes = 0; }
+    if (r->slot >= 0) { s->slot_busy[r->slot] = 0; r->slot = -1; }
+}
+
+void scheduler(svd_server_s* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        bool progressed = false;
+        // completions
+        for (size_t i = 0; i < s->running.size();) {
+            Request* r = s->running[i];
+            const cudaError_t q = cudaEventQuery(r->done_ev);
+            if (q == cudaErrorNotReady) { ++i; continue; }
+            svd_status st = q == cudaSuccess ? svd_sync(r->plan) : SVD_ERR_CUDA;
+            if (q != cudaSuccess) cudaGetLastError();
+            release(s, r);
+            finish(s, r, st);
+            s->running.erase(s->running.begin() + i);
+            progressed = true;
+        }
+        // admissions, in arrival order: reserve a slot and pool memory
+        std::vector<Request*> admitted;
+        while (!s->pending.empty()) {
+            Request* r = s->pending.front();
+            int slot = -1;
+            for (int i = 0; i < s->max_inflight; ++i)
+                if (!s->slot_busy[i]) { slot = i; break; }
+            if (slot < 0) break;
+            if (r->inject_alloc) {
+                s->pending.pop_front();
+                finish(s, r, SVD_ERR_OOM);
+                progressed = true;
+                continue;
+            }
+            size_t off = 0;
+            if (!s->pool->alloc(r->total_bytes, &off)) break;   // wait for memory
+            s->pending.pop_front();
+            r->off = off;
+            r->slot = slot;
+            s->slot_busy[slot] = 1;
+            r->t_admit = now_s();
+            r->state = kRunning;
+            admitted.push_back(r);
+        }
+        if (!admitted.empty()) {
+            // enqueue their work without holding the lock
+            lk.unlock();
+            std::vector<svd_status> res(admitted.size());
+            for (size_t i = 0; i < admitted.size(); ++i) {
+                res[i] = start(s, admitted[i]);
+                // a request that failed part-way may still have copies in flight
+                // on its stream: let them land before its memory is reused
+                if (res[i] != SVD_OK) cudaStreamSynchronize(s->streams[admitted[i]->slot]);
+            }
+            lk.lock();
+            for (size_t i = 0; i < admitted.size(); ++i) {
+                Request* r = admitted[i];
+                if (res[i] == SVD_OK) {
+                    s->running.push_back(r);
+                } else {
+                    release(s, r);
+                    finish(s, r, res[i]);
+                }
+            }
+            progressed = true;
+        }
+        if (progressed) s->cv_done.notify_all();
+        if (s->stop && s->running.empty() && s->pending.empty()) break;
+        if (!progressed) {
+            if (s->running.empty() && !s->stop)
+                s->cv_work.wait(lk);
+            else
+                s->cv_work.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+svd_status svd_server_create(size_t budget_bytes, int32_t max_inflight, svd_server_t* out) {
+    if (!out || budget_bytes < 4096 || max_inflight < 1 || max_inflight > 256)
+        return SVD_ERR_INVALID_ARG;
+    *out = nullptr;
+    svd_server_s* s = new (std::nothrow) svd_server_s();
+    if (!s) return SVD_ERR_OOM;
+    cudaGetDevice(&s->device);
+    s->budget = budget_bytes & ~(size_t)255;
+    if (cudaMalloc(&s->base, s->budget) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return SVD_ERR_OOM;
+    }
+    s->pool = new Pool(s->budget);
+    s->max_inflight = max_inflight;
+    s->streams.resize(max_inflight);
+    s->slot_busy.assign(max_inflight, 0);
+    for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    s->worker = std::thread(scheduler, s);
+    *out = s;
+    return SVD_OK;
+}
+
+svd_status svd_server_submit(svd_server_t s, const svd_request* req, uint64_t* ticket) {
+    if (!s || !req || !ticket || !req->h_col_ptr || !req->h_sigma || !req->h_U || !req->h_rank)
+        return SVD_ERR_INVALID_ARG;
+    size_t plan_bytes = 0;
+    svd_status st = svd_plan_bytes(&req->desc, &plan_bytes);
+    if (st != SVD_OK) return st;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return SVD_ERR_OOM;
+    r->desc = req->desc;
+    if (req->desc.block_col_bounds) {
+        r->bounds.assign(req->desc.block_col_bounds,
+                         req->desc.block_col_bounds + req->desc.num_blocks + 1);
+        r->desc.block_col_bounds = r->bounds.data();
+    }
+    r->io = *req;
+    r->plan_bytes = plan_bytes;
+    r->total_bytes = layout(r->desc, plan_bytes).total;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (r->total_bytes > s->budget) {
+        ++s->n_rejected;
+        delete r;
+        return SVD_ERR_BUDGET;
+    }
+    if (cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete r;
+        return SVD_ERR_CUDA;
+    }
+    r->ticket = s->next_ticket++;
+    auto inj = s->injections.find(r->ticket);
+    if (inj != s->injections.end()) {
+        r->inject_alloc = inj->second == SVD_INJECT_ALLOC;
+        r->inject_bad_csc = inj->second == SVD_INJECT_BAD_CSC;
+        if (r->inject_bad_csc) r->desc.flags |= SVD_FLAG_CHECK_CSC;
+        s->injections.erase(inj);
+    }
+    r->t_submit = now_s();
+    s->pending.push_back(r);
+    s->all[r->ticket] = r;
+    ++s->n_submitted;
+    *ticket = r->ticket;
+    s->cv_work.notify_one();
+    return SVD_OK;
+}
+
+svd_status svd_server_poll(svd_server_t s, uint64_t ticket, int32_t* done, svd_status* result) {
+    if (!s || !done) return SVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return SVD_ERR_INVALID_ARG;
+    *done = it->second->state == kDone;
+    if (result) *result = it->second->result;
+    return SVD_OK;
+}
+
+svd_status svd_server_wait(svd_server_t s, uint64_t ticket, double timeout_s, svd_status* result) {
+    if (!s) return SVD_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return SVD_ERR_INVALID_ARG;
+    Request* r = it->second;
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                              std::chrono::duration<double>(std::max(timeout_s, 0.0)));
+    while (r->state != kDone) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state != kDone)
+            return SVD_ERR_TIMEOUT;
+    }
+    if (result) *result = r->result;
+    return SVD_OK;
+}
+
+svd_status svd_server_cancel(svd_server_t s, uint64_t ticket) {
+    if (!s) return SVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return SVD_ERR_INVALID_ARG;
+    Request* r = it->second;
+    if (r->state != kPending) return SVD_ERR_INVALID_ARG;   // only queued requests
+    s->pending.erase(std::remove(s->pending.begin(), s->pending.end(), r), s->pending.end());
+    r->state = kDone;
+    r->result = SVD_ERR_INVALID_ARG;
+    r->t_done = now_s();
+    ++s->n_failed;
+    s->cv_done.notify_all();
+    return SVD_OK;
+}
+
+svd_status svd_server_times(svd_server_t s, uint64_t ticket, double* t_submit, double* t_admit,
+                            double* t_done) {
+    if (!s) return SVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return SVD_ERR_INVALID_ARG;
+    if (t_submit) *t_submit = it->second->t_submit;
+    if (t_admit) *t_admit = it->second->t_admit;
+    if (t_done) *t_done = it->second->t_done;
+    return SVD_OK;
+}
+
+svd_status svd_server_release(svd_server_t s, uint64_t ticket) {
+    if (!s) return SVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end() || it->second->state != kDone) return SVD_ERR_INVALID_ARG;
+    if (it->second->done_ev) cudaEventDestroy(it->second->done_ev);
+    delete it->second;
+    s->all.erase(it);
+    return SVD_OK;
+}
+
+svd_status svd_server_inject(svd_server_t s, int32_t what, uint64_t ticket) {
+    if (!s || (what != SVD_INJECT_ALLOC && what != SVD_INJECT_BAD_CSC)) return SVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->injections[ticket] = what;
+    return SVD_OK;
+}
+
+svd_status svd_server_stats(svd_server_t s, int64_t* out8) {
+    if (!s || !out8) return SVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out8[0] = s->n_submitted;
+    out8[1] = s->n_completed;
+    out8[2] = s->n_failed;
+    out8[3] = s->n_rejected;
+    out8[4] = (int64_t)s->running.size();
+    out8[5] = (int64_t)s->pending.size();
+    out8[6] = (int64_t)s->pool->used();
+    out8[7] = (int64_t)s->pool->peak();
+    return SVD_OK;
+}
+
+void svd_server_destroy(svd_server_t s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        // queued requests are dropped; running ones finish first
+        for (Request* r : s->pending) {
+            r->state = kDone;
+            r->result = SVD_ERR_INVALID_ARG;
+        }
+        s->pending.clear();
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& kv : s->all) {
+        if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+        delete kv.second;
+    }
+    for (auto& st : s->streams) cudaStreamDestroy(st);
+    cudaFree(s->base);
+    delete s->pool;
+    delete s;
+}
+
+}  // extern "C"

@@ -91,13 +91,33 @@ def _distinct_rows(rng: np.random.Generator, M: int, degrees: np.ndarray,
 
 
 def bernoulli_csc(rng: np.random.Generator, M: int, N: int, density: float):
-    """Bernoulli(density) pattern, drawn column by column: degree ~ Bin(M, p),
-    rows uniform without replacement.  Returns (col_ptr, row_idx)."""
-    deg = rng.binomial(M, density, size=N).astype(np.int64)
-    c, r = _distinct_rows(rng, M, deg)
+    """Bernoulli(density) pattern over the M x N entries, column-major.  The
+    positions of the successes of the Bernoulli sequence are drawn as
+    cumulative geometric gaps, which gives exactly the Bernoulli law and comes
+    out sorted by (column, row).  Returns (col_ptr, row_idx)."""
+    total = M * N
+    if density <= 0.0 or total == 0:
+        return np.zeros(N + 1, dtype=np.int64), np.zeros(0, dtype=np.int32)
+    if density >= 1.0:
+        pos = np.arange(total, dtype=np.int64)
+    else:
+        parts, last = [], -1
+        while True:
+            remaining = total - 1 - last
+            draw = int(remaining * density + 6.0 * np.sqrt(remaining * density + 1.0) + 64)
+            gaps = rng.geometric(density, size=draw).astype(np.int64)
+            pos = last + np.cumsum(gaps)
+            if pos[-1] >= total:
+                parts.append(pos[pos < total])
+                break
+            parts.append(pos)
+            last = int(pos[-1])
+        pos = np.concatenate(parts)
+    cols = pos // M
+    rows = (pos % M).astype(np.int32)
     col_ptr = np.zeros(N + 1, dtype=np.int64)
-    np.cumsum(deg, out=col_ptr[1:])
-    return col_ptr, r.astype(np.int32)
+    np.cumsum(np.bincount(cols, minlength=N), out=col_ptr[1:])
+    return col_ptr, rows
 
 
 def small_uniform(seed: int = SEED_BASE + 1) -> CscCase:

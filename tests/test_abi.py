@@ -24,7 +24,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:svd_status|void|const char\*|int32_t)\s+(svd_\w+)\s*\(", text,
+    names = re.findall(r"^\s*(?:svd_status|void|const char\*|int32_t|int64_t)\s+(svd_\w+)\s*\(", text,
                        flags=re.M)
     return sorted(set(names))
 
