@@ -103,6 +103,14 @@ typedef struct {
 #define SVD_FLAG_CHECK_CSC 1   /* svd_run validates the CSC first (synchronous) */
 #define SVD_FLAG_SKIP_V 2      /* do not compute V (d_V may be NULL) */
 #define SVD_FLAG_TIMING 4      /* record per-stage CUDA events (SVD_Q_STAGE_MS) */
+#define SVD_FLAG_DENSE_REFINE 8 /* mixed precision: form the block refinement's G X^T from the
+                                 dense block cross product even when the sparse columns
+                                 would be cheaper (both give the same result up to
+                                 rounding; for testing and timing) */
+#define SVD_FLAG_FP64_PRODUCTS 16 /* mixed precision: form the refinement products and
+                                 P P^T with FP64 arithmetic instead of exact 8-bit
+                                 slices on the bf16 tensor cores (for testing and
+                                 timing) */
 
 /* One RandomChecker insertion: A'[row, col] = 1.0 (Algorithm 2). */
 typedef struct {

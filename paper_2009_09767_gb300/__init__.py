@@ -33,6 +33,8 @@ VALUE = {"f32": 0, "f64": 1}
 FLAG_CHECK_CSC = 1
 FLAG_SKIP_V = 2
 FLAG_TIMING = 4
+FLAG_DENSE_REFINE = 8
+FLAG_FP64_PRODUCTS = 16
 STAGES = ["partition", "gram", "block_jacobi", "block_refine", "sort_proxy", "merge_gram",
           "merge_eig", "finalize", "spmm"]
 

@@ -79,6 +79,10 @@ struct svd_plan_s {
     double* SR1 = nullptr;
     double* SR2 = nullptr;
     double* SR3 = nullptr;
+    // exact-slice operands of the tensor-core products (mixed precision)
+    bool use_oz = false;
+    uint16_t* oz_sl[2] = {nullptr, nullptr};
+    unsigned long long* oz_amax[2] = {nullptr, nullptr};
     double* slam = nullptr;
     double* snorm = nullptr;
     double* msig = nullptr;
@@ -199,6 +203,15 @@ void carve(svd_plan_s* p, Carver& c) {
         p->Sw64 = c.take<double>(mm);
         p->W64 = c.take<double>((size_t)M * std::max(p->k, 1));
     }
+    if (p->use_oz) {
+        const int64_t blk = p->refine_iters > 0 ? oz_operand_elems(D, 5, Mp, Mp) : 0;
+        const int64_t mrg = std::max(oz_operand_elems(1, 5, M, p->Rmax), oz_operand_elems(1, 5, Mp, Mp));
+        const int64_t rows = round_up(Mp, OZ_ROW_PAD);
+        p->oz_sl[0] = c.take<uint16_t>((size_t)std::max(blk, mrg));
+        p->oz_sl[1] = c.take<uint16_t>((size_t)std::max(blk, oz_operand_elems(1, 5, Mp, Mp)));
+        p->oz_amax[0] = c.take<unsigned long long>((size_t)D * rows);
+        p->oz_amax[1] = c.take<unsigned long long>((size_t)D * rows);
+    }
     p->msig = c.take<double>(M);
     p->mperm = c.take<int32_t>(M);
     p->mrank = c.take<int32_t>(1);
@@ -216,6 +229,7 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
     p->k = d->k > 0 ? d->k : (int)std::min<int64_t>(d->M, d->N);
     p->mixed = d->precision == SVD_PREC_MIXED;
     p->random = d->rank_fix == SVD_RANKFIX_RANDOM;
+    p->use_oz = p->mixed && !(d->flags & SVD_FLAG_FP64_PRODUCTS);
     p->Mp = jacobi_pad(d->M);
     p->W = (d->M + 31) / 32;
     p->max_sweeps = d->max_sweeps > 0 ? d->max_sweeps : 40;
@@ -349,9 +363,22 @@ svd_status block_jacobi(svd_plan_s* p, cudaStream_t s) {
     return SVD_OK;
 }
 
+// Kernels one refinement step launches (see launch_refine): the sparse
+// route adds the transpose of X and the scatter, the exact-slice products
+// two kernels per operand split.
+int refine_launches(bool sparse, bool oz, int nchunks) {
+    const int scatter = sparse && nchunks > 0 ? 1 : 0;
+    if (oz) return sparse ? 15 + scatter : 16;
+    return sparse ? 7 + scatter : 7;
+}
+
+void oz_ops(svd_plan_s* p, OzOperand* ops) {
+    for (int i = 0; i < 2; ++i) ops[i] = OzOperand{p->oz_sl[i], p->oz_amax[i], 0, 0, 0, 0};
+}
+
 // Block refinement, sort and rank, proxy P and P P^T (Eqs. 2-3); leaves the
 // merge matrix for the merge eigensolve.
-svd_status phase_mid(svd_plan_s* p, cudaStream_t s) {
+svd_status phase_mid(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
     const int D = p->D, M = p->M, Mp = p->Mp;
     const int64_t mm = (int64_t)Mp * Mp;
     mark(p, 3, s);
@@ -365,9 +392,20 @@ svd_status phase_mid(svd_plan_s* p, cudaStream_t s) {
         LAUNCH(p, 1, launch_convert_f32_f64(p->Vt32, p->Vt64, (int64_t)D * mm, s));
         double* X = p->Vt64;
         double* Xn = p->Xn;
+        // G X^T straight from the sparse blocks when that is cheaper than the
+        // dense product (no insertions: those are only in the dense G)
+        // (2 nnz Mp FP64 loads and atomics against D Mp^3 multiply-adds)
+        const bool sparse = !p->random && !(p->d.flags & SVD_FLAG_DENSE_REFINE) &&
+                            8.0 * (double)p->nnz < (double)D * Mp * (double)Mp;
+        const SparseBlocks sb{io.col_ptr, io.row_idx, io.vals, p->d.value_type, p->nchunks,
+                              p->chunk_block, p->chunk_lo, p->chunk_hi};
+        OzOperand oz[2];
+        oz_ops(p, oz);
         for (int it = 0; it < p->refine_iters; ++it) {
-            LAUNCH(p, 7, launch_refine(p->G64, X, Xn, p->lam, D, Mp, p->RW1, p->RW2, p->RW3,
-                                       p->norms, s));
+            LAUNCH(p, refine_launches(sparse, p->use_oz, p->nchunks),
+                   launch_refine(p->G64, X, Xn, p->lam, D, Mp, p->RW1, p->RW2, p->RW3,
+                                       p->norms, s, sparse ? &sb : nullptr,
+                                       p->use_oz ? oz : nullptr));
             std::swap(X, Xn);
         }
         LAUNCH(p, 1, launch_sort_rank(p->lam, nullptr, nullptr, nullptr, D, M, Mp, p->bounds_d, 0,
@@ -382,8 +420,10 @@ svd_status phase_mid(svd_plan_s* p, cudaStream_t s) {
     LAUNCH(p, 2, launch_proxy(Xblk64, Xblk32, p->bsig, p->bperm, p->brank, D, M, Mp, p->pofs, p->P,
                               s));
     mark(p, 5, s);
-    LAUNCH(p, 2, launch_merge_gram(p->P, p->pofs, D, M, Mp, p->Rmax, p->partial, p->nsplit,
-                                   p->S64, s));
+    OzOperand oz[2];
+    oz_ops(p, oz);
+    LAUNCH(p, p->use_oz ? 4 : 2, launch_merge_gram(p->P, p->pofs, D, M, Mp, p->Rmax, p->partial, p->nsplit,
+                                   p->S64, s, p->use_oz ? oz : nullptr));
     mark(p, 6, s);
     if (!p->mixed)
         CU(cudaMemcpyAsync(p->Sw64, p->S64, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
@@ -416,9 +456,12 @@ svd_status phase_post(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         LAUNCH(p, 1, launch_convert_f32_f64(p->SV32, p->SV64, mm, s));
         double* X = p->SV64;
         double* Xn = p->SXn;
+        OzOperand oz[2];
+        oz_ops(p, oz);
         for (int it = 0; it < p->merge_refine_iters; ++it) {
-            LAUNCH(p, 7, launch_refine(p->S64, X, Xn, p->slam, 1, Mp, p->SR1, p->SR2, p->SR3,
-                                       p->snorm, s));
+            LAUNCH(p, refine_launches(false, p->use_oz, 0),
+                   launch_refine(p->S64, X, Xn, p->slam, 1, Mp, p->SR1, p->SR2, p->SR3,
+                                       p->snorm, s, nullptr, p->use_oz ? oz : nullptr));
             std::swap(X, Xn);
         }
         LAUNCH(p, 1, launch_sort_rank(p->slam, nullptr, nullptr, nullptr, 1, M, Mp, nullptr, p->N,
@@ -460,7 +503,7 @@ svd_status run_device(svd_plan_s* p, const int64_t* col_ptr, const int32_t* row_
     const RunIO io{col_ptr, row_idx, vals, d_sigma, d_U, d_V, d_rank, d_patches, d_npatches};
     svd_status st = phase_pre(p, io, s);
     if (st == SVD_OK) st = block_jacobi(p, s);
-    if (st == SVD_OK) st = phase_mid(p, s);
+    if (st == SVD_OK) st = phase_mid(p, io, s);
     if (st == SVD_OK) st = merge_jacobi(p, s);
     if (st == SVD_OK) st = phase_post(p, io, s);
     return st;
@@ -861,7 +904,8 @@ svd_status batch_enqueue(svd_batch_s* b, const RunIO* ios, cudaStream_t s) {
     for (int i : b->outsized)
         if ((st = block_jacobi(b->plans[i], s)) != SVD_OK) return st;
     fork(b, s);
-    for (size_t i = 0; i < n && st == SVD_OK; ++i) st = phase_mid(b->plans[i], b->streams[i % ns]);
+    for (size_t i = 0; i < n && st == SVD_OK; ++i)
+        st = phase_mid(b->plans[i], ios[i], b->streams[i % ns]);
     join(b, s);
     if (st != SVD_OK) return st;
     if ((st = batch_items(b, 2, s)) != SVD_OK) return st;

@@ -232,16 +232,116 @@ __global__ void k_oa_E(double* __restrict__ W1, const double* __restrict__ W3, i
 }
 }  // namespace
 
+// T = G X^T from the sparse block instead of the dense G (G = sum_j a_j a_j^T
+// over the block's columns): T = sum_j a_j (X a_j)^T.  One warp per column j
+// forms y = X a_j from the rows of X^T picked by the column's entries, then
+// adds v_e * y to row r_e of T for every entry (r_e, v_e) (FP64 atomics).
+// Cost 2 * nnz * Mp multiply-adds instead of the dense Mp^3.
+namespace {
+constexpr int kYPerLane = 8;   // FP64 accumulators per lane (256 columns of T per pass)
+
+__global__ void __launch_bounds__(256)
+k_transpose(const double* __restrict__ X, double* __restrict__ XT, int Mp) {
+    __shared__ double tile[32][33];
+    const int64_t off = (int64_t)blockIdx.z * Mp * Mp;
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) tile[r][tx] = X[off + (int64_t)(by + r) * Mp + bx + tx];
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) XT[off + (int64_t)(bx + r) * Mp + by + tx] = tile[tx][r];
+}
+
+__global__ void __launch_bounds__(256)
+k_sparse_gxt(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+             const void* __restrict__ vals, int value_type, int Mp,
+             const int32_t* __restrict__ chunk_block, const int64_t* __restrict__ chunk_lo,
+             const int64_t* __restrict__ chunk_hi, const double* __restrict__ XT,
+             double* __restrict__ T) {
+    const int c = blockIdx.x;
+    const int d = chunk_block[c];
+    const int64_t mm = (int64_t)Mp * Mp;
+    const double* XTd = XT + d * mm;
+    double* Td = T + d * mm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t j = chunk_lo[c] + warp; j < chunk_hi[c]; j += 8) {
+        const int64_t e0 = col_ptr[j], e1 = col_ptr[j + 1];
+        if (e0 == e1) continue;
+        for (int i0 = 0; i0 < Mp; i0 += 32 * kYPerLane) {
+            double y[kYPerLane];
+#pragma unroll
+            for (int q = 0; q < kYPerLane; ++q) y[q] = 0.0;
+            for (int64_t e = e0; e < e1; ++e) {
+                const double v = load_val(vals, value_type, e);
+                const double* xr = XTd + (int64_t)row_idx[e] * Mp + i0 + lane;
+#pragma unroll
+                for (int q = 0; q < kYPerLane; ++q)
+                    if (i0 + lane + 32 * q < Mp) y[q] = fma(v, xr[32 * q], y[q]);
+            }
+            for (int64_t e = e0; e < e1; ++e) {
+                const double v = load_val(vals, value_type, e);
+                double* tr = Td + (int64_t)row_idx[e] * Mp + i0 + lane;
+#pragma unroll
+                for (int q = 0; q < kYPerLane; ++q)
+                    if (i0 + lane + 32 * q < Mp) atomicAdd(tr + 32 * q, v * y[q]);
+            }
+        }
+    }
+}
+}  // namespace
+
 cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* lam, int nmat,
                           int Mp, double* W1, double* W2, double* W3, double* norms,
-                          cudaStream_t s) {
+                          cudaStream_t s, const SparseBlocks* sp, OzOperand* oz) {
     const int64_t st = (int64_t)Mp * Mp;
-    // W1 = X X^T (symmetric)
-    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, X, Mp, st, 1, 0.0, W1, Mp, st, s, 1));
-    // W2 = X G
-    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, G, Mp, st, 0, 0.0, W2, Mp, st, s));
-    // W3 = W2 X^T = X G X^T (symmetric)
-    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W2, Mp, st, 0, X, Mp, st, 1, 0.0, W3, Mp, st, s, 1));
+    if (sp) {
+        // X^T staged in W3 for the sparse product
+        k_transpose<<<dim3(Mp / 32, Mp / 32, nmat), 256, 0, s>>>(X, W3, Mp);
+        RK_CUDA_TRY(cudaGetLastError());
+    }
+    if (oz) {
+        // exact-slice products (oz[0], oz[1] hold the operands): X sliced once
+        // for W1 = X X^T and S = X (G X^T)
+        OzOperand& xa = oz[0];
+        OzOperand& ob = oz[1];
+        RK_CUDA_TRY(launch_oz_split(nmat, Mp, Mp, X, Mp, st, 0, nullptr, 5, xa, s));
+        RK_CUDA_TRY(launch_oz_gemm(nmat, Mp, Mp, xa, xa, 1.0, 0.0, W1, Mp, st, 1, s));
+        if (sp) {
+            // W2 = T = G X^T from the sparse columns; W3 = X T (B rows = columns of T)
+            RK_CUDA_TRY(cudaMemsetAsync(W2, 0, sizeof(double) * st * nmat, s));
+            if (sp->nchunks > 0) {
+                k_sparse_gxt<<<sp->nchunks, 256, 0, s>>>(sp->col_ptr, sp->row_idx, sp->vals,
+                                                         sp->value_type, Mp, sp->chunk_block,
+                                                         sp->chunk_lo, sp->chunk_hi, W3, W2);
+                RK_CUDA_TRY(cudaGetLastError());
+            }
+            RK_CUDA_TRY(launch_oz_split(nmat, Mp, Mp, W2, Mp, st, 1, nullptr, 5, ob, s));
+            RK_CUDA_TRY(launch_oz_gemm(nmat, Mp, Mp, xa, ob, 1.0, 0.0, W3, Mp, st, 1, s));
+        } else {
+            // W2 = X G (G symmetric: its rows are the B rows), W3 = W2 X^T
+            RK_CUDA_TRY(launch_oz_split(nmat, Mp, Mp, G, Mp, st, 0, nullptr, 5, ob, s));
+            RK_CUDA_TRY(launch_oz_gemm(nmat, Mp, Mp, xa, ob, 1.0, 0.0, W2, Mp, st, 0, s));
+            RK_CUDA_TRY(launch_oz_split(nmat, Mp, Mp, W2, Mp, st, 0, nullptr, 5, ob, s));
+            RK_CUDA_TRY(launch_oz_gemm(nmat, Mp, Mp, ob, xa, 1.0, 0.0, W3, Mp, st, 1, s));
+        }
+    } else {
+        // W1 = X X^T (symmetric)
+        RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, X, Mp, st, 1, 0.0, W1, Mp, st, s, 1));
+        if (sp) {
+            // W2 = G X^T from the sparse blocks (X^T in W3), then W3 = X W2
+            RK_CUDA_TRY(cudaMemsetAsync(W2, 0, sizeof(double) * st * nmat, s));
+            if (sp->nchunks > 0) {
+                k_sparse_gxt<<<sp->nchunks, 256, 0, s>>>(sp->col_ptr, sp->row_idx, sp->vals,
+                                                         sp->value_type, Mp, sp->chunk_block,
+                                                         sp->chunk_lo, sp->chunk_hi, W3, W2);
+                RK_CUDA_TRY(cudaGetLastError());
+            }
+            RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, W2, Mp, st, 0, 0.0, W3, Mp, st, s, 1));
+        } else {
+            // W2 = X G, W3 = W2 X^T = X G X^T (symmetric)
+            RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, X, Mp, st, 0, G, Mp, st, 0, 0.0, W2, Mp, st, s));
+            RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W2, Mp, st, 0, X, Mp, st, 1, 0.0, W3, Mp, st, s, 1));
+        }
+    }
     k_oa_norms<<<nmat, 512, 0, s>>>(W1, W3, Mp, lam, norms);
     RK_CUDA_TRY(cudaGetLastError());
     const int bx = (int)std::min<int64_t>(ceil_div(st, 256), 1024);
@@ -249,7 +349,14 @@ cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* 
     RK_CUDA_TRY(cudaGetLastError());
     // Xn = X + E^T X
     RK_CUDA_TRY(cudaMemcpyAsync(Xn, X, sizeof(double) * st * nmat, cudaMemcpyDeviceToDevice, s));
-    RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W1, Mp, st, 1, X, Mp, st, 0, 1.0, Xn, Mp, st, s));
+    if (oz) {
+        // the correction is small: three slices (relative 2^-23) are ample
+        RK_CUDA_TRY(launch_oz_split(nmat, Mp, Mp, W1, Mp, st, 1, nullptr, 3, oz[0], s));
+        RK_CUDA_TRY(launch_oz_split(nmat, Mp, Mp, X, Mp, st, 1, nullptr, 3, oz[1], s));
+        RK_CUDA_TRY(launch_oz_gemm(nmat, Mp, Mp, oz[0], oz[1], 1.0, 1.0, Xn, Mp, st, 0, s));
+    } else {
+        RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W1, Mp, st, 1, X, Mp, st, 0, 1.0, Xn, Mp, st, s));
+    }
     const int64_t rows = (int64_t)nmat * Mp;
     k_normalize_rows<<<(unsigned)ceil_div(rows * 32, 256), 256, 0, s>>>(Xn, Mp, rows);
     return cudaGetLastError();
@@ -455,12 +562,19 @@ int merge_gram_splits(int M, int64_t Rmax) {
 
 cudaError_t launch_merge_gram(const double* P, const int64_t* proxy_ofs, int D, int M, int Mp,
                               int64_t Rmax, double* partial, int nsplit, double* S,
-                              cudaStream_t s) {
-    const int ntile = (M + GT - 1) / GT;
-    const int upper = ntile * (ntile + 1) / 2;
-    const int64_t kc = round_up(ceil_div(Rmax, nsplit), GK);
-    k_merge_partial<<<dim3(upper, nsplit), 256, 0, s>>>(P, proxy_ofs, D, M, kc, partial, Mp);
-    RK_CUDA_TRY(cudaGetLastError());
+                              cudaStream_t s, OzOperand* oz) {
+    if (oz) {
+        // exact-slice product over the proxy columns (P is column-major M x R)
+        RK_CUDA_TRY(launch_oz_split(1, M, Rmax, P, M, 0, 1, proxy_ofs + D, 5, *oz, s));
+        RK_CUDA_TRY(launch_oz_gemm(1, M, M, *oz, *oz, 1.0, 0.0, partial, Mp, 0, 1, s, nsplit,
+                                   (int64_t)Mp * Mp));
+    } else {
+        const int ntile = (M + GT - 1) / GT;
+        const int upper = ntile * (ntile + 1) / 2;
+        const int64_t kc = round_up(ceil_div(Rmax, nsplit), GK);
+        k_merge_partial<<<dim3(upper, nsplit), 256, 0, s>>>(P, proxy_ofs, D, M, kc, partial, Mp);
+        RK_CUDA_TRY(cudaGetLastError());
+    }
     const int64_t n = (int64_t)Mp * Mp;
     const int bx = (int)std::min<int64_t>(ceil_div(n, 256), 2048);
     k_merge_reduce<<<bx, 256, 0, s>>>(partial, nsplit, M, Mp, S);

@@ -72,12 +72,54 @@ cudaError_t launch_dgemm(int nb, int m, int n, int k, double alpha, const double
                          int64_t strideA, int tA, const double* B, int64_t ldb, int64_t strideB,
                          int tB, double beta, double* C, int64_t ldc, int64_t strideC,
                          cudaStream_t s, int sym = 0);
+// FP64-accurate products on the bf16 tensor cores (ozaki.cu).  An operand is
+// a stack of S integer slices (bf16 bits) per row with the row's magnitude
+// bound, rows padded to OZ_ROW_PAD and k to OZ_K_PAD (zeros).
+constexpr int OZ_ROW_PAD = 128;
+constexpr int OZ_K_PAD = 32;
+struct OzOperand {
+    uint16_t* slices;                // [nb][S][rows_pad][kpad]
+    unsigned long long* amax;        // [nb][rows_pad] bits of max |x| per row
+    int S;
+    int rows;
+    int rows_pad;
+    int64_t kpad;
+};
+int64_t oz_operand_elems(int nb, int S, int rows, int64_t k);
+// Split nb matrices (rows x k logical; element (r, c) at src[r ld + c], or at
+// src[c ld + r] when trans) into S = 3 or 5 slices.  kdev, when given, holds
+// the number of valid k on the device (the rest reads as zero).
+cudaError_t launch_oz_split(int nb, int rows, int64_t k, const double* src, int64_t ld,
+                            int64_t stride, int trans, const int64_t* kdev, int S, OzOperand& op,
+                            cudaStream_t s);
+// C = alpha A B^T + beta C for nb matrices (m x n, row-major ldc).  With
+// nsplit > 1 the k range is split and split z writes C + z strideSplit (beta
+// then applies per split).  sym: only tiles on or above the diagonal are
+// formed and mirrored.
+cudaError_t launch_oz_gemm(int nb, int m, int n, const OzOperand& A, const OzOperand& B,
+                           double alpha, double beta, double* C, int64_t ldc, int64_t strideC,
+                           int sym, cudaStream_t s, int nsplit = 1, int64_t strideSplit = 0);
+// The sparse blocks behind block cross products (for G X^T without the dense G).
+struct SparseBlocks {
+    const int64_t* col_ptr;
+    const int32_t* row_idx;
+    const void* vals;
+    int value_type;
+    int nchunks;
+    const int32_t* chunk_block;
+    const int64_t* chunk_lo;
+    const int64_t* chunk_hi;
+};
 // One Ogita-Aishima refinement step for nmat symmetric matrices G with
 // approximate eigenvector rows X (Mp x Mp).  Xn receives the refined rows,
 // lam the eigenvalue estimates.  W1..W3 are Mp x Mp scratch per matrix.
+// With sp, G X^T is formed from the sparse columns (G itself unused); with
+// oz (two operand buffers of nmat x 5 slices x Mp x Mp) every product runs on
+// the tensor cores through exact slices instead of the FP64 pipes.
 cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* lam, int nmat,
                           int Mp, double* W1, double* W2, double* W3, double* norms,
-                          cudaStream_t s);
+                          cudaStream_t s, const SparseBlocks* sp = nullptr,
+                          OzOperand* oz = nullptr);
 // Per matrix: sort eigenvalues (lam, or the diagonal of Gdiag when lam is null)
 // of the first M indices descending, rank by tolerance, write sigma
 // (sqrt(max(lam,0))) sorted, the permutation and the rank.
@@ -91,7 +133,8 @@ cudaError_t launch_proxy(const double* X64, const float* X32, const double* sigm
                          int64_t* proxy_ofs, double* P, cudaStream_t s);
 // S = P P^T (M x M, stored Mp x Mp), split over the R columns.
 cudaError_t launch_merge_gram(const double* P, const int64_t* proxy_ofs, int D, int M, int Mp,
-                              int64_t Rmax, double* partial, int nsplit, double* S, cudaStream_t s);
+                              int64_t Rmax, double* partial, int nsplit, double* S, cudaStream_t s,
+                              OzOperand* oz = nullptr);
 int merge_gram_splits(int M, int64_t Rmax);
 // Final sort, sign rule, outputs and the SpMM weights W = U_k S_k^-1.
 cudaError_t launch_finalize(const double* X64, const float* X32, const double* sigma_sorted,

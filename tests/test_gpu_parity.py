@@ -248,3 +248,23 @@ def test_check_csc_rejects_malformed():
     assert lib.svd_check_csc(3, 2, 3, rk._ptr(good_cp), rk._ptr(out_of_range), s) == 2
     bad_end = torch.tensor([0, 2, 4], dtype=torch.int64, device=dev)
     assert lib.svd_check_csc(3, 2, 3, rk._ptr(bad_end), rk._ptr(good_ri), s) == 2
+
+
+@pytest.mark.parametrize("vdtype", [np.float64, np.float32])
+def test_sparse_block_refinement(vdtype):
+    """Mixed precision on a very sparse matrix: the block refinement forms
+    G X^T from the sparse columns (8 nnz < D Mp^2 here); forcing the dense
+    cross product instead must give the same spectrum and subspaces."""
+    case = _random_case(150, 40000, 0.0008, 4, seed=77, name="very_sparse")
+    Mp = 160
+    assert 8 * case.nnz < case.num_blocks * Mp * Mp
+    res = run_case(case, "mixed", vdtype=vdtype)
+    s_ref, _, _ = check_against_oracle(case, res, "mixed")
+    dev = torch.device("cuda")
+    vals = torch.from_numpy(np.ascontiguousarray(case.vals.astype(vdtype))).to(dev)
+    _, dense = rk.svd(torch.from_numpy(case.col_ptr).to(dev), torch.from_numpy(case.row_idx).to(dev),
+                      vals, case.M, case.N, case.num_blocks, precision="mixed",
+                      flags=rk.FLAG_DENSE_REFINE)
+    sd = dense["sigma"].cpu().numpy()
+    sigma_check(res["sigma"], sd, 1e-9, 1e-9 * sd[0])
+    subspace_check(res["U"], dense["U"].cpu().numpy(), sd, 1e-6)
