@@ -82,6 +82,8 @@ struct svd_plan_s {
     // exact-slice operands of the tensor-core products (mixed precision)
     bool use_oz = false;
     uint16_t* oz_sl[2] = {nullptr, nullptr};
+    // published pair rotations of the FP32 solver: D blocks, then the merge
+    char* jwork = nullptr;
     unsigned long long* oz_amax[2] = {nullptr, nullptr};
     double* slam = nullptr;
     double* snorm = nullptr;
@@ -170,6 +172,7 @@ void carve(svd_plan_s* p, Carver& c) {
     if (p->mixed) {
         p->G32 = c.take<float>((size_t)D * mm);
         p->Vt32 = c.take<float>((size_t)D * mm);
+        p->jwork = c.take<char>(jacobi_work_bytes(D + 1, Mp));
         if (p->refine_iters > 0) {
             p->Xn = c.take<double>((size_t)D * mm);
             p->RW1 = c.take<double>((size_t)D * mm);
@@ -359,7 +362,7 @@ svd_status block_jacobi(svd_plan_s* p, cudaStream_t s) {
                                            p->jac_tol, p->sweeps, s));
     else
         LAUNCH(p, 1, launch_jacobi<float>(p->G32, p->Vt32, p->D, p->Mp, p->max_sweeps, p->jac_tol,
-                                          p->sweeps, s));
+                                          p->sweeps, s, p->jwork));
     return SVD_OK;
 }
 
@@ -438,7 +441,8 @@ svd_status merge_jacobi(svd_plan_s* p, cudaStream_t s) {
                                            p->sweeps + p->D, s));
     else
         LAUNCH(p, 1, launch_jacobi<float>(p->S32, p->SV32, 1, p->Mp, p->max_sweeps, p->jac_tol,
-                                          p->sweeps + p->D, s));
+                                          p->sweeps + p->D, s,
+                                          p->jwork + jacobi_work_bytes(p->D, p->Mp)));
     return SVD_OK;
 }
 
@@ -965,6 +969,7 @@ svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, s
             it.G = f64 ? (void*)(p->Gw64 + d * mm) : (void*)(p->G32 + d * mm);
             it.Vt = f64 ? (void*)(p->Vt64 + d * mm) : (void*)(p->Vt32 + d * mm);
             it.sweeps = p->sweeps + d;
+            it.work = f64 ? nullptr : (void*)(p->jwork + jacobi_work_bytes(d, p->Mp));
             it.Mp = p->Mp;
             lists[wb].push_back(it);
         }
@@ -972,6 +977,7 @@ svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, s
         m.G = f64 ? (void*)p->Sw64 : (void*)p->S32;
         m.Vt = f64 ? (void*)p->SV64 : (void*)p->SV32;
         m.sweeps = p->sweeps + p->D;
+        m.work = f64 ? nullptr : (void*)(p->jwork + jacobi_work_bytes(p->D, p->Mp));
         m.Mp = p->Mp;
         lists[2 + wb].push_back(m);
         for (int w : {wb, 2 + wb}) {

@@ -26,6 +26,7 @@
 // size) and k_jacobi_items (persistent single-CTA workers that take matrices
 // of any size from a work list; used to batch many problems in one launch).
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -753,6 +754,466 @@ k_jacobi_items(const JacobiItem* __restrict__ items, int nitems, int* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 solver, symmetric block form.  The step's rotation is
+// J = diag(Q_1, ..., Q_np) over the pair index sets P_u = I_u + J_u, so the
+// new matrix is made of the 32 x 32 blocks
+//   G'[P_u, P_w] = Q_u^T G[P_u, P_w] Q_w          (u <= w, mirrored below)
+// and the eigenvector columns V'[:, P_u] = V[:, P_u] Q_u (V = Vt^T while the
+// solve runs).  Every block is one independent warp job: no shared-memory
+// staging and no CTA-wide barrier inside the update, one barrier after the
+// pair solves (their Q are published through L2) and one after the update.
+//
+// Products run on the tensor cores with f16 operands split as
+// hi = f16(x), lo = f16(x - hi) and accumulated as lo*hi + hi*lo + hi*hi
+// in FP32 (22 significant bits per operand, the same as a TF32 hi/lo split,
+// in half as many mma instructions).  The split keeps 22 bits only while lo
+// is a normal f16, i.e. for |x| >= 2^-3, so every operand is moved up the
+// f16 exponent range by a power of two (exact, removed in FP32): G is scaled
+// on entry so that its Gershgorin bound max_i sum_j |G_ij| (>= lambda_max,
+// which bounds every entry of every iterate; the diagonal alone does not:
+// it grows towards lambda_max as the solve proceeds) lies in [2^12, 2^13),
+// so that |Q^T G[P_u, P_w]| <= sqrt(32) 2^13 < 2^16 stays finite; Q and V
+// are split as 2^14 Q and 2^14 V.  Below 2^-3 of its scale an operand keeps an absolute
+// error of 2^-25 of that scale, far under the rotation floor; without the
+// shift that error reaches the floor and rotations never stop.  Q is
+// published as (2^14 Q)^T (row n = column n of Q), hi then lo, 32 x 32
+// halves each: both GEMM operands read from it as consecutive pairs.
+constexpr int kJT4 = 256;                      // threads per CTA
+constexpr int kW4 = kJT4 / 32;                 // warps per CTA
+constexpr int kQWords = kB2 * kB2 / 2;         // 32-bit words of one 32 x 32 f16 matrix
+constexpr float kQScale = 16384.f;             // 2^14: Q and V as split operands
+constexpr float kQInv = 1.f / 16384.f;
+
+struct J4Smem {
+    static constexpr int LD = kB2 + 1;
+    // per warp: sub-problem, its rotation, the round's rotation table
+    static constexpr size_t per_warp = sizeof(float) * (2 * kB2 * LD + 2 * kB) + sizeof(int) * 2 * kB;
+    static constexpr size_t bytes = per_warp * kW4;
+};
+
+__device__ __forceinline__ void split_h2(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(x, y);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += A B with A = ah + al, B = bh + bl (the al*bl term is below the split)
+__device__ __forceinline__ void mma_split(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                          uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_f16(d, al, bh0, bh1);
+    mma_f16(d, ah, bl0, bl1);
+    mma_f16(d, ah, bh0, bh1);
+}
+
+__device__ __forceinline__ uint32_t ldcg_u32(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ldcg_f2(const float* p) {
+    return __ldcg(reinterpret_cast<const float2*>(p));
+}
+
+// Fragment coordinates (m16n8k16): g = lane / 4, t = lane % 4;
+//   A (16 x 16): (g, 2t..2t+1) (g+8, 2t..) (g, 2t+8..) (g+8, 2t+8..)
+//   B (16 x 8):  (k = 2t..2t+1, n = g) (k = 2t+8.., n = g)
+//   C (16 x 8):  (g, 2t) (g, 2t+1) (g+8, 2t) (g+8, 2t+1)
+
+// Block job: G[P_u, P_w] <- Q_u^T G[P_u, P_w] Q_w and its mirror.  B of the
+// first product is read through the symmetry, B[k][n] = G[P_w(n)][P_u(k)],
+// so every fragment is a consecutive pair.  On the diagonal (u == w) only the
+// upper triangle is written, to both halves.
+__device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restrict__ Qu,
+                          const uint32_t* __restrict__ Qw, int ui, int uj, int wi, int wj) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const bool diag = ui == wi && uj == wj;
+    float acc[2][4][4];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+            for (int z = 0; z < 4; ++z) acc[x][y][z] = 0.f;
+    // T = Q_u^T B: A[m][k] = QT_u[m][k]
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const int m = mi * 16 + g, kp = kk * 8 + t;
+            ah[mi][0] = ldcg_u32(Qu + m * 16 + kp);
+            ah[mi][1] = ldcg_u32(Qu + (m + 8) * 16 + kp);
+            ah[mi][2] = ldcg_u32(Qu + m * 16 + kp + 4);
+            ah[mi][3] = ldcg_u32(Qu + (m + 8) * 16 + kp + 4);
+            al[mi][0] = ldcg_u32(Qu + kQWords + m * 16 + kp);
+            al[mi][1] = ldcg_u32(Qu + kQWords + (m + 8) * 16 + kp);
+            al[mi][2] = ldcg_u32(Qu + kQWords + m * 16 + kp + 4);
+            al[mi][3] = ldcg_u32(Qu + kQWords + (m + 8) * 16 + kp + 4);
+        }
+        const int k = kk * 16 + 2 * t;
+        const int c0 = gidx(ui, uj, k), c1 = gidx(ui, uj, k + 8);
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj) {
+            const float* row = G + (int64_t)gidx(wi, wj, nj * 8 + g) * Mp;
+            const float2 v0 = ldcg_f2(row + c0), v1 = ldcg_f2(row + c1);
+            uint32_t bh0, bl0, bh1, bl1;
+            split_h2(v0.x, v0.y, bh0, bl0);
+            split_h2(v1.x, v1.y, bh1, bl1);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) mma_split(acc[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
+        }
+    }
+    // out = T Q_w: A = T from the accumulators, B[k][n] = QT_w[n][k]
+    float out[2][4][4];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+            for (int z = 0; z < 4; ++z) out[x][y][z] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            // T = Q_u^T B: the accumulators hold 2^14 T
+            const float* c0 = acc[mi][2 * kk];
+            const float* c1 = acc[mi][2 * kk + 1];
+            split_h2(c0[0] * kQInv, c0[1] * kQInv, ah[mi][0], al[mi][0]);
+            split_h2(c0[2] * kQInv, c0[3] * kQInv, ah[mi][1], al[mi][1]);
+            split_h2(c1[0] * kQInv, c1[1] * kQInv, ah[mi][2], al[mi][2]);
+            split_h2(c1[2] * kQInv, c1[3] * kQInv, ah[mi][3], al[mi][3]);
+        }
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj) {
+            const int n = nj * 8 + g, kp = kk * 8 + t;
+            const uint32_t bh0 = ldcg_u32(Qw + n * 16 + kp), bh1 = ldcg_u32(Qw + n * 16 + kp + 4);
+            const uint32_t bl0 = ldcg_u32(Qw + kQWords + n * 16 + kp);
+            const uint32_t bl1 = ldcg_u32(Qw + kQWords + n * 16 + kp + 4);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) mma_split(out[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int hz = 0; hz < 2; ++hz) {
+            const int m = mi * 16 + g + 8 * hz;
+            const int gm = gidx(ui, uj, m);
+#pragma unroll
+            for (int nj = 0; nj < 4; ++nj) {
+                const int n = nj * 8 + 2 * t;
+                const int gn = gidx(wi, wj, n);       // n, n + 1 in the same half
+                const float v0 = out[mi][nj][2 * hz] * kQInv, v1 = out[mi][nj][2 * hz + 1] * kQInv;
+                if (!diag) {
+                    *reinterpret_cast<float2*>(G + (int64_t)gm * Mp + gn) = make_float2(v0, v1);
+                    G[(int64_t)gn * Mp + gm] = v0;
+                    G[(int64_t)(gn + 1) * Mp + gm] = v1;
+                } else {
+                    if (m <= n) {
+                        G[(int64_t)gm * Mp + gn] = v0;
+                        G[(int64_t)gn * Mp + gm] = v0;
+                    }
+                    if (m <= n + 1) {
+                        G[(int64_t)gm * Mp + gn + 1] = v1;
+                        G[(int64_t)(gn + 1) * Mp + gm] = v1;
+                    }
+                }
+            }
+        }
+}
+
+// Column job: V[r0..r0+31, P_u] <- V[r0..r0+31, P_u] Q_u.
+__device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restrict__ Qu, int ui,
+                          int uj, int r0) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float out[2][4][4];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+            for (int z = 0; z < 4; ++z) out[x][y][z] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = kk * 16 + 2 * t;
+        const int c0 = gidx(ui, uj, k), c1 = gidx(ui, uj, k + 8);
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const float* ra = V + (int64_t)(r0 + mi * 16 + g) * Mp;
+            const float* rb = ra + 8 * (int64_t)Mp;
+            const float2 x0 = ldcg_f2(ra + c0), x1 = ldcg_f2(rb + c0);
+            const float2 x2 = ldcg_f2(ra + c1), x3 = ldcg_f2(rb + c1);
+            split_h2(x0.x * kQScale, x0.y * kQScale, ah[mi][0], al[mi][0]);
+            split_h2(x1.x * kQScale, x1.y * kQScale, ah[mi][1], al[mi][1]);
+            split_h2(x2.x * kQScale, x2.y * kQScale, ah[mi][2], al[mi][2]);
+            split_h2(x3.x * kQScale, x3.y * kQScale, ah[mi][3], al[mi][3]);
+        }
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj) {
+            const int n = nj * 8 + g, kp = kk * 8 + t;
+            const uint32_t bh0 = ldcg_u32(Qu + n * 16 + kp), bh1 = ldcg_u32(Qu + n * 16 + kp + 4);
+            const uint32_t bl0 = ldcg_u32(Qu + kQWords + n * 16 + kp);
+            const uint32_t bl1 = ldcg_u32(Qu + kQWords + n * 16 + kp + 4);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) mma_split(out[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int hz = 0; hz < 2; ++hz) {
+            float* row = V + (int64_t)(r0 + mi * 16 + g + 8 * hz) * Mp;
+#pragma unroll
+            for (int nj = 0; nj < 4; ++nj) {
+                const int gn = gidx(ui, uj, nj * 8 + 2 * t);
+                *reinterpret_cast<float2*>(row + gn) =
+                    make_float2(out[mi][nj][2 * hz] * (kQInv * kQInv), out[mi][nj][2 * hz + 1] * (kQInv * kQInv));
+            }
+        }
+}
+
+// Solve one FP32 matrix with csize CTAs (rank crank); qbuf holds the np
+// published rotations (np x 2 x kQWords words).
+template <bool kCluster>
+__device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int Mp, int csize,
+                               int crank, int max_sweeps, float tol, int32_t* __restrict__ sweeps_out,
+                               uint32_t* __restrict__ qbuf, unsigned char* smem_raw) {
+    constexpr int LD = J4Smem::LD;
+    const int nb = Mp / kB, np = nb / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = csize * kW4, gwarp = crank * kW4 + warp;
+    float* sub = reinterpret_cast<float*>(smem_raw + J4Smem::per_warp * warp);
+    float* Q = sub + kB2 * LD;
+    float* rc = Q + kB2 * LD;
+    float* rs = rc + kB;
+    int* rp = reinterpret_cast<int*>(rs + kB);
+    int* rq = rp + kB;
+    __shared__ int rot_flag;
+    __shared__ int decision;
+    __shared__ float scale_sh, dmax_sh;
+
+    // scale: the Gershgorin bound max_i sum_j |G_ij| >= lambda_max, which
+    // bounds every entry the solve will produce, into [2^12, 2^13); the
+    // largest diagonal sets the rotation floor
+    __shared__ unsigned int rowsum_bits;
+    if (threadIdx.x == 0) rowsum_bits = 0u;
+    __syncthreads();
+    {
+        float rmax = 0.f;
+        for (int i = warp; i < Mp; i += kW4) {
+            float acc = 0.f;
+            for (int j = lane; j < Mp; j += 32) acc += fabsf(__ldcg(G + (int64_t)i * Mp + j));
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            rmax = fmaxf(rmax, acc);
+        }
+        if (lane == 0) atomicMax(&rowsum_bits, __float_as_uint(rmax));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float dmax = 0.f;
+        for (int i = lane; i < Mp; i += 32) dmax = fmaxf(dmax, fabsf(__ldcg(G + (int64_t)i * Mp + i)));
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (lane == 0) {
+            const float bound = __uint_as_float(rowsum_bits);
+            int e = 0;
+            if (bound > 0.f) frexpf(bound, &e);        // bound in [2^(e-1), 2^e)
+            scale_sh = bound > 0.f ? ldexpf(1.f, 13 - e) : 1.f;
+            dmax_sh = dmax * scale_sh;
+            rot_flag = 0;
+        }
+    }
+    __syncthreads();
+    const float sc = scale_sh;
+    // absolute floor of the rotation threshold (see the FP64 solver)
+    const float floor_abs = 4.f * (float)Eps<float>::value * dmax_sh;
+    owner_sync<kCluster>();
+    for (int64_t e = (int64_t)crank * kJT4 + threadIdx.x; e < (int64_t)Mp * Mp;
+         e += (int64_t)csize * kJT4) {
+        const int i = (int)(e / Mp), j = (int)(e % Mp);
+        V[e] = i == j ? 1.f : 0.f;
+        G[e] = __ldcg(G + e) * sc;
+    }
+    owner_sync<kCluster>();
+
+    const int nblk = np * (np + 1) / 2;
+    const int rtiles = Mp / kB2;
+    const int njobs = nblk + np * rtiles;
+    int sweep = 0;
+    bool converged = false;
+    while (sweep < max_sweeps) {
+        int rotated = 0;
+        for (int step = 0; step < nb - 1; ++step) {
+            // pair solves; each warp publishes Q^T (hi, lo) of its pairs
+            for (int u = gwarp; u < np; u += nwarps) {
+                int bi, bj;
+                circle_pair(nb, step, u, bi, bj);
+                for (int i = 0; i < kB2; ++i) {
+                    sub[i * LD + lane] = __ldcg(G + (int64_t)gidx(bi, bj, i) * Mp + gidx(bi, bj, lane));
+                    Q[i * LD + lane] = i == lane ? 1.f : 0.f;
+                }
+                __syncwarp();
+                warp_sweep<float>(sub, Q, rc, rs, rp, rq, tol, floor_abs, rotated);
+                __syncwarp();
+                uint32_t* qo = qbuf + (size_t)u * 2 * kQWords;
+#pragma unroll 4
+                for (int w = 0; w < kB; ++w) {
+                    // row n = lane of Q^T: Q[2w][lane], Q[2w + 1][lane]
+                    uint32_t hi, lo;
+                    split_h2(Q[(2 * w) * LD + lane] * kQScale, Q[(2 * w + 1) * LD + lane] * kQScale, hi, lo);
+                    qo[lane * 16 + w] = hi;
+                    qo[kQWords + lane * 16 + w] = lo;
+                }
+                __syncwarp();
+            }
+            owner_sync<kCluster>();
+            for (int j = gwarp; j < njobs; j += nwarps) {
+                int u, w2 = 0;
+                if (j < nblk) {
+                    int r = j;
+                    u = 0;
+                    while (r >= np - u) { r -= np - u; ++u; }
+                    w2 = u + r;
+                    int ui, uj, wi, wj;
+                    circle_pair(nb, step, u, ui, uj);
+                    circle_pair(nb, step, w2, wi, wj);
+                    job_block(G, Mp, qbuf + (size_t)u * 2 * kQWords, qbuf + (size_t)w2 * 2 * kQWords,
+                              ui, uj, wi, wj);
+                } else {
+                    const int r = j - nblk;
+                    u = r / rtiles;
+                    int ui, uj;
+                    circle_pair(nb, step, u, ui, uj);
+                    job_vcols(V, Mp, qbuf + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
+                }
+            }
+            owner_sync<kCluster>();
+        }
+        ++sweep;
+        if (__syncthreads_or(rotated) && threadIdx.x == 0) rot_flag = 1;
+        __syncthreads();
+        int any;
+        if constexpr (kCluster) {
+            cg::cluster_group cluster = cg::this_cluster();
+            if (crank == 0 && threadIdx.x == 0) {
+                int acc = 0;
+                for (int r = 0; r < csize; ++r) acc |= *cluster.map_shared_rank(&rot_flag, r);
+                decision = acc;
+            }
+            cluster.sync();
+            any = *cluster.map_shared_rank(&decision, 0);
+            cluster.sync();
+        } else {
+            any = rot_flag;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) rot_flag = 0;
+        __syncthreads();
+        if (!any) { converged = true; break; }
+    }
+    // unscale G; V^T into place as Vt (each unordered pair swapped once).
+    // Other CTAs wrote G and V: every load here goes through L2.
+    const float inv = 1.f / sc;
+    for (int64_t e = (int64_t)crank * kJT4 + threadIdx.x; e < (int64_t)Mp * Mp;
+         e += (int64_t)csize * kJT4) {
+        G[e] = __ldcg(G + e) * inv;
+        const int i = (int)(e / Mp), j = (int)(e % Mp);
+        if (i < j) {
+            const float a = __ldcg(V + e), b = __ldcg(V + (int64_t)j * Mp + i);
+            V[e] = b;
+            V[(int64_t)j * Mp + i] = a;
+        }
+    }
+    if (crank == 0 && threadIdx.x == 0) *sweeps_out = converged ? sweep : -sweep;
+}
+
+__global__ void __launch_bounds__(kJT4, 2)
+k_jacobi4(float* __restrict__ Gall, float* __restrict__ Vall, int Mp, int csize, int max_sweeps,
+          float tol, int32_t* __restrict__ sweeps_out, uint32_t* __restrict__ qall) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int crank = (int)cg::this_cluster().block_rank();
+    const int mat = blockIdx.x / csize;
+    const int np = Mp / kB2;
+    jacobi4_matrix<true>(Gall + (int64_t)mat * Mp * Mp, Vall + (int64_t)mat * Mp * Mp, Mp, csize,
+                         crank, max_sweeps, tol, sweeps_out + mat,
+                         qall + (size_t)mat * np * 2 * kQWords, smem_raw);
+}
+
+__global__ void __launch_bounds__(kJT4, 2)
+k_jacobi4_items(const JacobiItem* __restrict__ items, int nitems, int* __restrict__ next,
+                int max_sweeps, float tol) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int item_sh;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = item_sh;
+        __syncthreads();
+        if (it >= nitems) break;
+        const JacobiItem w = items[it];
+        jacobi4_matrix<false>(static_cast<float*>(w.G), static_cast<float*>(w.Vt), w.Mp, 1, 0,
+                              max_sweeps, tol, w.sweeps, static_cast<uint32_t*>(w.work), smem_raw);
+        __syncthreads();
+    }
+}
+
+// Cluster size of the FP32 solver: a step costs one pair solve (kSolve4 job
+// units) plus the jobs of one warp; clusters run in waves of the hardware's
+// maximum active clusters.
+constexpr int kSolve4 = 4;
+
+int pick_cluster4(int nmat, int Mp) {
+    const int np = Mp / kB2;
+    const int64_t jobs = (int64_t)np * (np + 1) / 2 + (int64_t)np * (Mp / kB2);
+    int best = -1;
+    double best_cost = 1e300;
+    for (int cs = 1; cs <= kMaxCluster; cs *= 2) {
+        if (cs > 8 && cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                          cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)J4Smem::bytes) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cs, 1, 1);
+        cfg.blockDim = dim3(kJT4, 1, 1);
+        cfg.dynamicSmemBytes = J4Smem::bytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi4, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const int nw = cs * kW4;
+        const double solves = (double)((np + nw - 1) / nw);
+        const double per_warp = (double)(jobs + nw - 1) / nw;
+        const int64_t waves = (nmat + nclusters - 1) / nclusters;
+        const double cost = (double)waves * (kSolve4 * solves + per_warp);
+        if (cost <= best_cost) { best_cost = cost; best = cs; }
+    }
+    return best;
+}
+
 // Cluster size for nmat matrices with npairs block pairs per step.  A CTA
 // owns ppc = ceil(npairs / csize) pairs; its step costs about one warp sweep
 // (the pairs' warps run in parallel) plus ppc pairs of panel products, so a
@@ -807,60 +1268,100 @@ int pick_cluster(int nmat, int npairs) {
 
 int jacobi_pad(int M) { return (int)round_up(M, kB2); }
 
-int jacobi_item_max_mp(bool fp64) { return kB2 * (fp64 ? PairsMax<double>::value : PairsMax<float>::value); }
+int jacobi_item_max_mp(bool fp64) { return fp64 ? kB2 * PairsMax<double>::value : kMaxM; }
+
+size_t jacobi_work_bytes(int nmat, int Mp) {
+    return (size_t)std::max(nmat, 0) * (Mp / kB2) * 2 * kQWords * sizeof(uint32_t);
+}
 
 template <typename T>
 cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
-                          int32_t* sweeps, cudaStream_t s) {
+                          int32_t* sweeps, cudaStream_t s, void* work) {
     if (nmat <= 0) return cudaSuccess;
     if (Mp % kB2 != 0) return cudaErrorInvalidValue;
     const int npairs = Mp / kB2;
-    const int csize = pick_cluster<T>(nmat, npairs);
-    if (csize < 1) return cudaErrorInvalidConfiguration;
-    const int ppc = (npairs + csize - 1) / csize;
-    const size_t smem = JSmem<T>::bytes(ppc);
-    auto kern = k_jacobi<T>;
-    if (csize > 8)
-        RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(nmat * csize), 1, 1);
-    cfg.blockDim = dim3(kJT, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)csize;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, G, Vt, Mp, csize, ppc, max_sweeps, (T)tol, sweeps);
+    if constexpr (sizeof(T) == 4) {
+        if (!work) return cudaErrorInvalidValue;
+        const int csize = pick_cluster4(nmat, Mp);
+        if (csize < 1) return cudaErrorInvalidConfiguration;
+        if (csize > 8)
+            RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)J4Smem::bytes));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nmat * csize), 1, 1);
+        cfg.blockDim = dim3(kJT4, 1, 1);
+        cfg.dynamicSmemBytes = J4Smem::bytes;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_jacobi4, (float*)G, (float*)Vt, Mp, csize, max_sweeps,
+                                  (float)tol, sweeps, static_cast<uint32_t*>(work));
+    } else {
+        const int csize = pick_cluster<T>(nmat, npairs);
+        if (csize < 1) return cudaErrorInvalidConfiguration;
+        const int ppc = (npairs + csize - 1) / csize;
+        const size_t smem = JSmem<T>::bytes(ppc);
+        auto kern = k_jacobi<T>;
+        if (csize > 8)
+            RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nmat * csize), 1, 1);
+        cfg.blockDim = dim3(kJT, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, G, Vt, Mp, csize, ppc, max_sweeps, (T)tol, sweeps);
+    }
 }
 
 template <typename T>
 cudaError_t launch_jacobi_items(const JacobiItem* items, int nitems, int max_mp, int* next,
                                 int max_sweeps, double tol, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    const int ppc = max_mp / kB2;
-    if (max_mp % kB2 != 0 || ppc < 1 || ppc > PairsMax<T>::value) return cudaErrorInvalidValue;
-    const size_t smem = JSmem<T>::bytes(ppc);
-    auto kern = k_jacobi_items<T>;
-    RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     RK_CUDA_TRY(cudaGetDevice(&dev));
     RK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    RK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJT, smem));
-    const int grid = std::max(1, std::min(nitems, sms * std::max(per_sm, 1)));
-    RK_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
-    k_jacobi_items<T><<<grid, kJT, smem, s>>>(items, nitems, next, max_sweeps, (T)tol);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        if (max_mp % kB2 != 0 || max_mp < kB2 || max_mp > kMaxM) return cudaErrorInvalidValue;
+        RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4_items, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)J4Smem::bytes));
+        RK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi4_items, kJT4,
+                                                                  J4Smem::bytes));
+        const int grid = std::max(1, std::min(nitems, sms * std::max(per_sm, 1)));
+        RK_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
+        k_jacobi4_items<<<grid, kJT4, J4Smem::bytes, s>>>(items, nitems, next, max_sweeps, (float)tol);
+        return cudaGetLastError();
+    } else {
+        const int ppc = max_mp / kB2;
+        if (max_mp % kB2 != 0 || ppc < 1 || ppc > PairsMax<T>::value) return cudaErrorInvalidValue;
+        const size_t smem = JSmem<T>::bytes(ppc);
+        auto kern = k_jacobi_items<T>;
+        RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJT, smem));
+        const int grid = std::max(1, std::min(nitems, sms * std::max(per_sm, 1)));
+        RK_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
+        k_jacobi_items<T><<<grid, kJT, smem, s>>>(items, nitems, next, max_sweeps, (T)tol);
+        return cudaGetLastError();
+    }
 }
 
 template cudaError_t launch_jacobi<float>(float*, float*, int, int, int, double, int32_t*,
-                                          cudaStream_t);
+                                          cudaStream_t, void*);
 template cudaError_t launch_jacobi<double>(double*, double*, int, int, int, double, int32_t*,
-                                           cudaStream_t);
+                                           cudaStream_t, void*);
 template cudaError_t launch_jacobi_items<float>(const JacobiItem*, int, int, int*, int, double,
                                                 cudaStream_t);
 template cudaError_t launch_jacobi_items<double>(const JacobiItem*, int, int, int*, int, double,

@@ -42,10 +42,13 @@ cudaError_t launch_convert_f32_f64(const float* src, double* dst, int64_t n, cud
 // ---- jacobi.cu: block two-sided Jacobi eigensolver ----------------------------
 // G (nmat x Mp x Mp, symmetric, overwritten by its diagonalised form) and
 // Vt (nmat x Mp x Mp, rows = eigenvectors on exit).  sweeps[mat] receives the
-// sweep count, negative when max_sweeps ran out.
+// sweep count, negative when max_sweeps ran out.  The FP32 solver needs
+// work = jacobi_work_bytes(nmat, Mp) bytes of device memory (the published
+// pair rotations); the FP64 one ignores it.
 template <typename T>
 cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
-                          int32_t* sweeps, cudaStream_t s);
+                          int32_t* sweeps, cudaStream_t s, void* work = nullptr);
+size_t jacobi_work_bytes(int nmat, int Mp);
 // Padded order of an M x M problem (a multiple of 32).
 int jacobi_pad(int M);
 
@@ -55,6 +58,7 @@ struct JacobiItem {
     void* G;
     void* Vt;
     int32_t* sweeps;
+    void* work;        // FP32: jacobi_work_bytes(1, Mp) bytes
     int32_t Mp;
     int32_t pad;
 };
