@@ -983,6 +983,140 @@ __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restr
         }
 }
 
+// One cyclic sweep of a 32 x 32 FP32 sub-problem by a group of K warps
+// (named barrier bar, 32 K threads), accumulating Q.  Warp 0 of the group
+// computes the round's 16 rotations (lanes 0..15) and, at the start of the
+// next round, writes the exact 2 x 2 diagonal blocks of the rotated pairs;
+// the row pass and the column pass (sub and Q) are split over the K warps
+// by pair.  The rotation parameters use the fast reciprocal and square root
+// (the angle only steers convergence); c is polished by one Newton step so
+// that c^2 + s^2 = 1 to about an ulp (orthogonality of Q).
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int K>
+__device__ void group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp, int* rq, float tol,
+                            float floor_abs, int& rotated, int wi, int bar) {
+    constexpr int LD = J4Smem::LD;
+    constexpr int NU = kB / K;                 // pairs per warp per pass
+    constexpr int HB = NU > 8 ? 8 : NU;        // pairs held in registers at once
+    const int lane = threadIdx.x & 31;
+    const float tol2 = tol * tol;
+    float fa = 0.f, fd = 0.f;
+    int fp = -1, fq = 0;
+    for (int r = 0; r < kB2 - 1; ++r) {
+        if (wi == 0) {
+            if (fp >= 0) {
+                sub[fp * LD + fp] = fa;
+                sub[fq * LD + fq] = fd;
+                sub[fp * LD + fq] = 0.f;
+                sub[fq * LD + fp] = 0.f;
+            }
+            __syncwarp();
+            if (lane < kB) {
+                int p, q;
+                circle_pair(kB2, r, lane, p, q);
+                const float a = sub[p * LD + p], d = sub[q * LD + q], g = sub[p * LD + q];
+                float c = 1.f, sn = 0.f;
+                fp = -1;
+                if (fabsf(g) > floor_abs && g * g > tol2 * fabsf(a * d)) {
+                    const float zeta = __fdividef(d - a, 2.f * g);
+                    const float az = fabsf(zeta);
+                    float t = az < 1e18f ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f)))
+                                         : __frcp_rn(2.f * az);
+                    if (zeta < 0.f) t = -t;
+                    const float x = fmaf(t, t, 1.f);
+                    c = rsqrtf(x);
+                    c = c * fmaf(-0.5f * x, c * c, 1.5f);
+                    sn = t * c;
+                    fa = a - t * g;
+                    fd = d + t * g;
+                    fp = p;
+                    fq = q;
+                    rotated = 1;
+                }
+                rc[lane] = c; rs[lane] = sn; rp[lane] = p; rq[lane] = q;
+            }
+        }
+        group_bar(bar, 32 * K);
+        // rows p, q (lane = column)
+#pragma unroll
+        for (int h = 0; h < NU; h += HB) {
+            float cu[HB], su[HB], x[HB], y[HB];
+            int pu[HB], qu[HB];
+#pragma unroll
+            for (int v = 0; v < HB; ++v) {
+                const int u = wi + (h + v) * K;
+                cu[v] = rc[u]; su[v] = rs[u]; pu[v] = rp[u]; qu[v] = rq[u];
+            }
+#pragma unroll
+            for (int v = 0; v < HB; ++v) { x[v] = sub[pu[v] * LD + lane]; y[v] = sub[qu[v] * LD + lane]; }
+#pragma unroll
+            for (int v = 0; v < HB; ++v) {
+                sub[pu[v] * LD + lane] = cu[v] * x[v] - su[v] * y[v];
+                sub[qu[v] * LD + lane] = su[v] * x[v] + cu[v] * y[v];
+            }
+        }
+        group_bar(bar, 32 * K);
+        // columns p, q of sub and of Q (lane = row)
+#pragma unroll
+        for (int h = 0; h < NU; h += HB) {
+            float cu[HB], su[HB], x[HB], y[HB];
+            int pu[HB], qu[HB];
+#pragma unroll
+            for (int v = 0; v < HB; ++v) {
+                const int u = wi + (h + v) * K;
+                cu[v] = rc[u]; su[v] = rs[u]; pu[v] = rp[u]; qu[v] = rq[u];
+            }
+#pragma unroll
+            for (int v = 0; v < HB; ++v) { x[v] = sub[lane * LD + pu[v]]; y[v] = sub[lane * LD + qu[v]]; }
+#pragma unroll
+            for (int v = 0; v < HB; ++v) {
+                sub[lane * LD + pu[v]] = cu[v] * x[v] - su[v] * y[v];
+                sub[lane * LD + qu[v]] = su[v] * x[v] + cu[v] * y[v];
+            }
+#pragma unroll
+            for (int v = 0; v < HB; ++v) { x[v] = Q[lane * LD + pu[v]]; y[v] = Q[lane * LD + qu[v]]; }
+#pragma unroll
+            for (int v = 0; v < HB; ++v) {
+                Q[lane * LD + pu[v]] = cu[v] * x[v] - su[v] * y[v];
+                Q[lane * LD + qu[v]] = su[v] * x[v] + cu[v] * y[v];
+            }
+        }
+        group_bar(bar, 32 * K);
+    }
+    // (the last round's exact diagonal is not needed: the block is rebuilt
+    // from the rotations by the update jobs)
+}
+
+// Load, solve and publish pair u with a group of K warps.
+template <int K>
+__device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step, int u, float* sub,
+                           float* Q, float* rc, float* rs, int* rp, int* rq, float tol,
+                           float floor_abs, int& rotated, int wi, int bar,
+                           uint32_t* __restrict__ qbuf) {
+    constexpr int LD = J4Smem::LD;
+    const int lane = threadIdx.x & 31;
+    int bi, bj;
+    circle_pair(nb, step, u, bi, bj);
+    for (int i = wi; i < kB2; i += K) {
+        sub[i * LD + lane] = __ldcg(G + (int64_t)gidx(bi, bj, i) * Mp + gidx(bi, bj, lane));
+        Q[i * LD + lane] = i == lane ? 1.f : 0.f;
+    }
+    group_bar(bar, 32 * K);
+    group_sweep<K>(sub, Q, rc, rs, rp, rq, tol, floor_abs, rotated, wi, bar);
+    uint32_t* qo = qbuf + (size_t)u * 2 * kQWords;
+    for (int w = wi; w < kB; w += K) {
+        // row n = lane of (2^14 Q)^T: Q[2w][lane], Q[2w + 1][lane]
+        uint32_t hi, lo;
+        split_h2(Q[(2 * w) * LD + lane] * kQScale, Q[(2 * w + 1) * LD + lane] * kQScale, hi, lo);
+        qo[lane * 16 + w] = hi;
+        qo[kQWords + lane * 16 + w] = lo;
+    }
+    group_bar(bar, 32 * K);
+}
+
 // Solve one FP32 matrix with csize CTAs (rank crank); qbuf holds the np
 // published rotations (np x 2 x kQWords words).
 template <bool kCluster>
@@ -993,12 +1127,6 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     const int nb = Mp / kB, np = nb / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = csize * kW4, gwarp = crank * kW4 + warp;
-    float* sub = reinterpret_cast<float*>(smem_raw + J4Smem::per_warp * warp);
-    float* Q = sub + kB2 * LD;
-    float* rc = Q + kB2 * LD;
-    float* rs = rc + kB;
-    int* rp = reinterpret_cast<int*>(rs + kB);
-    int* rq = rp + kB;
     __shared__ int rot_flag;
     __shared__ int decision;
     __shared__ float scale_sh, dmax_sh;
@@ -1046,6 +1174,10 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     }
     owner_sync<kCluster>();
 
+    // groups of kgrp warps share one pair solve (kgrp * pairs of this CTA <= 8)
+    const int nmine = (np - crank + csize - 1) / csize;
+    const int kgrp = nmine >= kW4 ? 1 : nmine >= 4 ? 2 : nmine >= 2 ? 4 : 8;
+    const int ngroups = kW4 / kgrp, grp = warp / kgrp, wi = warp % kgrp;
     const int nblk = np * (np + 1) / 2;
     const int rtiles = Mp / kB2;
     const int njobs = nblk + np * rtiles;
@@ -1054,27 +1186,22 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     while (sweep < max_sweeps) {
         int rotated = 0;
         for (int step = 0; step < nb - 1; ++step) {
-            // pair solves; each warp publishes Q^T (hi, lo) of its pairs
-            for (int u = gwarp; u < np; u += nwarps) {
-                int bi, bj;
-                circle_pair(nb, step, u, bi, bj);
-                for (int i = 0; i < kB2; ++i) {
-                    sub[i * LD + lane] = __ldcg(G + (int64_t)gidx(bi, bj, i) * Mp + gidx(bi, bj, lane));
-                    Q[i * LD + lane] = i == lane ? 1.f : 0.f;
+            // pair solves: the CTA's pairs u = crank + t csize go to groups of
+            // kgrp warps; each group publishes (2^14 Q)^T (hi, lo) of its pairs
+            for (int t = grp; t < nmine; t += ngroups) {
+                const int u = crank + t * csize;
+                float* gsub = reinterpret_cast<float*>(smem_raw + J4Smem::per_warp * grp);
+                float* gQ = gsub + kB2 * LD;
+                float* grc = gQ + kB2 * LD;
+                float* grs = grc + kB;
+                int* grp_p = reinterpret_cast<int*>(grs + kB);
+                int* grp_q = grp_p + kB;
+                switch (kgrp) {
+                    case 1: solve_pair<1>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
+                    case 2: solve_pair<2>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
+                    case 4: solve_pair<4>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
+                    default: solve_pair<8>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
                 }
-                __syncwarp();
-                warp_sweep<float>(sub, Q, rc, rs, rp, rq, tol, floor_abs, rotated);
-                __syncwarp();
-                uint32_t* qo = qbuf + (size_t)u * 2 * kQWords;
-#pragma unroll 4
-                for (int w = 0; w < kB; ++w) {
-                    // row n = lane of Q^T: Q[2w][lane], Q[2w + 1][lane]
-                    uint32_t hi, lo;
-                    split_h2(Q[(2 * w) * LD + lane] * kQScale, Q[(2 * w + 1) * LD + lane] * kQScale, hi, lo);
-                    qo[lane * 16 + w] = hi;
-                    qo[kQWords + lane * 16 + w] = lo;
-                }
-                __syncwarp();
             }
             owner_sync<kCluster>();
             for (int j = gwarp; j < njobs; j += nwarps) {
