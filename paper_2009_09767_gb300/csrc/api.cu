@@ -396,10 +396,14 @@ svd_status phase_mid(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         double* X = p->Vt64;
         double* Xn = p->Xn;
         // G X^T straight from the sparse blocks when that is cheaper than the
-        // dense product (no insertions: those are only in the dense G)
-        // (2 nnz Mp FP64 loads and atomics against D Mp^3 multiply-adds)
+        // dense product (no insertions: those are only in the dense G).  The
+        // scatter costs 2 nnz Mp FP64 loads and atomics; the dense route D Mp^3
+        // multiply-adds, on the tensor cores with the exact-slice products
+        // (measured: one scatter update costs about as much as 100 dense
+        // multiply-adds there), on the FP64 pipes otherwise (about 8).
+        const double dense_per_nnz = p->use_oz ? 100.0 : 8.0;
         const bool sparse = !p->random && !(p->d.flags & SVD_FLAG_DENSE_REFINE) &&
-                            8.0 * (double)p->nnz < (double)D * Mp * (double)Mp;
+                            dense_per_nnz * (double)p->nnz < (double)D * Mp * (double)Mp;
         const SparseBlocks sb{io.col_ptr, io.row_idx, io.vals, p->d.value_type, p->nchunks,
                               p->chunk_block, p->chunk_lo, p->chunk_hi};
         OzOperand oz[2];

@@ -788,9 +788,15 @@ constexpr float kQInv = 1.f / 16384.f;
 struct J4Smem {
     static constexpr int LD = kB2 + 1;
     // per warp: sub-problem, its rotation, the round's rotation table
-    static constexpr size_t per_warp = sizeof(float) * (2 * kB2 * LD + 2 * kB) + sizeof(int) * 2 * kB;
+    static constexpr size_t per_warp = sizeof(float) * (2 * kB2 * LD + 2 * kB) + sizeof(int) * (2 * kB + 4);
     static constexpr size_t bytes = per_warp * kW4;
 };
+
+// 32-bit words of solver work per matrix: np published rotations (2 kQWords
+// words each) and np identity flags, rounded to 256 bytes.
+__host__ __device__ inline size_t jwork_words(int Mp) {
+    return (size_t)round_up((int64_t)(Mp / kB2) * (2 * kQWords + 1), 64);
+}
 
 __device__ __forceinline__ void split_h2(float x, float y, uint32_t& hi, uint32_t& lo) {
     const __half2 h = __floats2half2_rn(x, y);
@@ -996,8 +1002,8 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
 }
 
 template <int K>
-__device__ void group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp, int* rq, float tol,
-                            float floor_abs, int& rotated, int wi, int bar) {
+__device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp, int* rq, int* act,
+                            float tol, float floor_abs, int& rotated, int wi, int bar) {
     constexpr int LD = J4Smem::LD;
     constexpr int NU = kB / K;                 // pairs per warp per pass
     constexpr int HB = NU > 8 ? 8 : NU;        // pairs held in registers at once
@@ -1005,6 +1011,7 @@ __device__ void group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
     const float tol2 = tol * tol;
     float fa = 0.f, fd = 0.f;
     int fp = -1, fq = 0;
+    bool any_round = false;
     for (int r = 0; r < kB2 - 1; ++r) {
         if (wi == 0) {
             if (fp >= 0) {
@@ -1021,7 +1028,7 @@ __device__ void group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
                 float c = 1.f, sn = 0.f;
                 fp = -1;
                 if (fabsf(g) > floor_abs && g * g > tol2 * fabsf(a * d)) {
-                    const float zeta = __fdividef(d - a, 2.f * g);
+                    const float zeta = (d - a) / (2.f * g);
                     const float az = fabsf(zeta);
                     float t = az < 1e18f ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f)))
                                          : __frcp_rn(2.f * az);
@@ -1038,8 +1045,17 @@ __device__ void group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
                 }
                 rc[lane] = c; rs[lane] = sn; rp[lane] = p; rq[lane] = q;
             }
+            // a round without any rotation leaves sub and Q unchanged.  The
+            // flag alternates between two slots by round parity: a warp still
+            // reading round r's slot cannot see round r + 1's write, and
+            // round r + 2 cannot start before every warp passed round r + 1's
+            // barrier.
+            const unsigned m = __ballot_sync(0xffffffffu, lane < kB && fp >= 0);
+            if (lane == 0) act[r & 1] = m != 0u;
         }
         group_bar(bar, 32 * K);
+        if (!act[r & 1]) continue;   // uniform over the group
+        any_round = true;
         // rows p, q (lane = column)
 #pragma unroll
         for (int h = 0; h < NU; h += HB) {
@@ -1088,14 +1104,16 @@ __device__ void group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
     }
     // (the last round's exact diagonal is not needed: the block is rebuilt
     // from the rotations by the update jobs)
+    group_bar(bar, 32 * K);    // every warp has read the flags before they are reused
+    return any_round;
 }
 
 // Load, solve and publish pair u with a group of K warps.
 template <int K>
 __device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step, int u, float* sub,
-                           float* Q, float* rc, float* rs, int* rp, int* rq, float tol,
+                           float* Q, float* rc, float* rs, int* rp, int* rq, int* act, float tol,
                            float floor_abs, int& rotated, int wi, int bar,
-                           uint32_t* __restrict__ qbuf) {
+                           uint32_t* __restrict__ qbuf, int* __restrict__ ident) {
     constexpr int LD = J4Smem::LD;
     const int lane = threadIdx.x & 31;
     int bi, bj;
@@ -1105,7 +1123,8 @@ __device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step
         Q[i * LD + lane] = i == lane ? 1.f : 0.f;
     }
     group_bar(bar, 32 * K);
-    group_sweep<K>(sub, Q, rc, rs, rp, rq, tol, floor_abs, rotated, wi, bar);
+    const bool moved = group_sweep<K>(sub, Q, rc, rs, rp, rq, act, tol, floor_abs, rotated, wi, bar);
+    if (wi == 0 && (threadIdx.x & 31) == 0) ident[u] = moved ? 0 : 1;
     uint32_t* qo = qbuf + (size_t)u * 2 * kQWords;
     for (int w = wi; w < kB; w += K) {
         // row n = lane of (2^14 Q)^T: Q[2w][lane], Q[2w + 1][lane]
@@ -1178,6 +1197,7 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     const int nmine = (np - crank + csize - 1) / csize;
     const int kgrp = nmine >= kW4 ? 1 : nmine >= 4 ? 2 : nmine >= 2 ? 4 : 8;
     const int ngroups = kW4 / kgrp, grp = warp / kgrp, wi = warp % kgrp;
+    int* ident = reinterpret_cast<int*>(qbuf + (size_t)np * 2 * kQWords);   // np flags
     const int nblk = np * (np + 1) / 2;
     const int rtiles = Mp / kB2;
     const int njobs = nblk + np * rtiles;
@@ -1196,11 +1216,12 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                 float* grs = grc + kB;
                 int* grp_p = reinterpret_cast<int*>(grs + kB);
                 int* grp_q = grp_p + kB;
+                int* gact = grp_q + kB;
                 switch (kgrp) {
-                    case 1: solve_pair<1>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
-                    case 2: solve_pair<2>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
-                    case 4: solve_pair<4>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
-                    default: solve_pair<8>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, tol, floor_abs, rotated, wi, 1 + grp, qbuf); break;
+                    case 1: solve_pair<1>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    case 2: solve_pair<2>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    case 4: solve_pair<4>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    default: solve_pair<8>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
                 }
             }
             owner_sync<kCluster>();
@@ -1211,14 +1232,17 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                     u = 0;
                     while (r >= np - u) { r -= np - u; ++u; }
                     w2 = u + r;
-                    int ui, uj, wi, wj;
+                    // both rotations the identity: the block does not change
+                    if (__ldcg(ident + u) && __ldcg(ident + w2)) continue;
+                    int ui, uj, wi2, wj;
                     circle_pair(nb, step, u, ui, uj);
-                    circle_pair(nb, step, w2, wi, wj);
+                    circle_pair(nb, step, w2, wi2, wj);
                     job_block(G, Mp, qbuf + (size_t)u * 2 * kQWords, qbuf + (size_t)w2 * 2 * kQWords,
-                              ui, uj, wi, wj);
+                              ui, uj, wi2, wj);
                 } else {
                     const int r = j - nblk;
                     u = r / rtiles;
+                    if (__ldcg(ident + u)) continue;
                     int ui, uj;
                     circle_pair(nb, step, u, ui, uj);
                     job_vcols(V, Mp, qbuf + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
@@ -1273,7 +1297,7 @@ k_jacobi4(float* __restrict__ Gall, float* __restrict__ Vall, int Mp, int csize,
     const int np = Mp / kB2;
     jacobi4_matrix<true>(Gall + (int64_t)mat * Mp * Mp, Vall + (int64_t)mat * Mp * Mp, Mp, csize,
                          crank, max_sweeps, tol, sweeps_out + mat,
-                         qall + (size_t)mat * np * 2 * kQWords, smem_raw);
+                         qall + (size_t)mat * jwork_words(Mp), smem_raw);
 }
 
 __global__ void __launch_bounds__(kJT4, 2)
@@ -1398,7 +1422,7 @@ int jacobi_pad(int M) { return (int)round_up(M, kB2); }
 int jacobi_item_max_mp(bool fp64) { return fp64 ? kB2 * PairsMax<double>::value : kMaxM; }
 
 size_t jacobi_work_bytes(int nmat, int Mp) {
-    return (size_t)std::max(nmat, 0) * (Mp / kB2) * 2 * kQWords * sizeof(uint32_t);
+    return (size_t)std::max(nmat, 0) * jwork_words(Mp) * sizeof(uint32_t);
 }
 
 template <typename T>
