@@ -7,6 +7,7 @@
 // FP64 arithmetic on this part runs on the FP64 pipes, whose rate is far below
 // the FP32 one, so every product here is compute-bound at any tile shape that
 // keeps the operands in shared memory.
+#include <cooperative_groups.h>
 #include <cfloat>
 
 #include <algorithm>
@@ -117,37 +118,52 @@ namespace {
 // iteration's underestimate.
 constexpr int kPowerIters = 8;
 
-__global__ void __launch_bounds__(512)
-k_oa_norms(const double* __restrict__ W1, const double* __restrict__ W3, int Mp,
+// One matrix per cluster of CS CTAs (CS <= 16): CTA c owns rows
+// [c Mp / CS, (c + 1) Mp / CS) of both matrices and computes that chunk of
+// every product; the chunks and the partial norms are exchanged through the
+// cluster's shared memory.  Every CTA keeps the whole iterate.
+__global__ void __launch_bounds__(256)
+k_oa_norms(const double* __restrict__ W1, const double* __restrict__ W3, int Mp, int CS,
            double* __restrict__ lam, double* __restrict__ norms) {
-    const int mat = blockIdx.x;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const int mat = blockIdx.x / CS;
     const double* XX = W1 + (int64_t)mat * Mp * Mp;
     const double* S = W3 + (int64_t)mat * Mp * Mp;
     double* L = lam + (int64_t)mat * Mp;
-    __shared__ float vs[kMaxM], vr[kMaxM], ys[kMaxM], yr[kMaxM];
-    __shared__ float red[2][16];
-    __shared__ double lmax_sh[16];
+    const int rows = Mp / CS, r0 = crank * rows;
+    __shared__ float vs[kMaxM], vr[kMaxM];
+    __shared__ float ys[kMaxM], yr[kMaxM];     // this CTA's chunk (first `rows` entries)
+    __shared__ double lrow[kMaxM];
+    __shared__ float part[3][8];
+    __shared__ float pnorm[3];                  // this CTA's |y_s|^2, |y_r|^2, lmax
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double lmax = 0.0;
-    for (int i = threadIdx.x; i < Mp; i += 512) {
+    float lmax = 0.f;
+    for (int q = threadIdx.x; q < rows; q += 256) {
+        const int i = r0 + q;
         const double xx = XX[(int64_t)i * Mp + i];
         const double l = xx > 0.0 ? S[(int64_t)i * Mp + i] / xx : 0.0;
         L[i] = l;
-        lmax = fmax(lmax, fabs(l));
+        lrow[q] = l;
+        lmax = fmaxf(lmax, (float)fabs(l));
+    }
+    for (int i = threadIdx.x; i < Mp; i += 256) {
         // deterministic start vector with all components non-zero
         const float v0 = 1.0f + 0.5f * (float)((i * 2654435761u) >> 28) / 16.0f;
         vs[i] = v0;
         vr[i] = v0;
     }
-    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    if (lane == 0) lmax_sh[warp] = lmax;
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if (lane == 0) part[2][warp] = lmax;
     __syncthreads();
     float ns = 0.f, nr = 0.f;
     for (int it = 0; it < kPowerIters; ++it) {
-        // y = B v for B = S - diag(lam) and B = -offdiag(X X^T), one warp per row
-        for (int i = warp; i < Mp; i += 16) {
+        // y = B v on this CTA's rows, B = S - diag(lam) and B = -offdiag(X X^T)
+        for (int q = warp; q < rows; q += 8) {
+            const int i = r0 + q;
             float as = 0.f, ar = 0.f;
-            const double li = L[i];
+            const double li = lrow[q];
             for (int j = lane; j < Mp; j += 32) {
                 const double s_ij = S[(int64_t)i * Mp + j] - (i == j ? li : 0.0);
                 const double r_ij = i == j ? 0.0 : -XX[(int64_t)i * Mp + j];
@@ -158,44 +174,51 @@ k_oa_norms(const double* __restrict__ W1, const double* __restrict__ W3, int Mp,
                 as += __shfl_xor_sync(0xffffffffu, as, o);
                 ar += __shfl_xor_sync(0xffffffffu, ar, o);
             }
-            if (lane == 0) { ys[i] = as; yr[i] = ar; }
+            if (lane == 0) { ys[q] = as; yr[q] = ar; }
         }
         __syncthreads();
+        // partial |y|^2 of the chunk; |v|^2 from the whole local iterate
         float ps = 0.f, pr = 0.f, qs = 0.f, qr = 0.f;
-        for (int i = threadIdx.x; i < Mp; i += 512) {
-            ps += ys[i] * ys[i]; pr += yr[i] * yr[i];
-            qs += vs[i] * vs[i]; qr += vr[i] * vr[i];
-        }
+        for (int q = threadIdx.x; q < rows; q += 256) { ps += ys[q] * ys[q]; pr += yr[q] * yr[q]; }
+        for (int i = threadIdx.x; i < Mp; i += 256) { qs += vs[i] * vs[i]; qr += vr[i] * vr[i]; }
         for (int o = 16; o > 0; o >>= 1) {
             ps += __shfl_xor_sync(0xffffffffu, ps, o); pr += __shfl_xor_sync(0xffffffffu, pr, o);
             qs += __shfl_xor_sync(0xffffffffu, qs, o); qr += __shfl_xor_sync(0xffffffffu, qr, o);
         }
-        __shared__ float part[4][16];
-        if (lane == 0) { part[0][warp] = ps; part[1][warp] = pr; part[2][warp] = qs; part[3][warp] = qr; }
+        __shared__ float pv[2][8];
+        if (lane == 0) { part[0][warp] = ps; part[1][warp] = pr; pv[0][warp] = qs; pv[1][warp] = qr; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
-            for (int w = 0; w < 16; ++w) { a += part[0][w]; b += part[1][w]; c += part[2][w]; d += part[3][w]; }
-            red[0][0] = c > 0.f ? sqrtf(a / c) : 0.f;   // |B v| / |v|
-            red[1][0] = d > 0.f ? sqrtf(b / d) : 0.f;
-            red[0][1] = a > 0.f ? rsqrtf(a) : 0.f;      // normalisers
-            red[1][1] = b > 0.f ? rsqrtf(b) : 0.f;
+            float a = 0.f, b = 0.f, lm = 0.f;
+            for (int w = 0; w < 8; ++w) { a += part[0][w]; b += part[1][w]; lm = fmaxf(lm, part[2][w]); }
+            pnorm[0] = a; pnorm[1] = b; pnorm[2] = lm;
         }
-        __syncthreads();
-        ns = red[0][0];
-        nr = red[1][0];
-        const float fs = red[0][1], fr = red[1][1];
-        for (int i = threadIdx.x; i < Mp; i += 512) {
-            vs[i] = ys[i] * fs;
-            vr[i] = yr[i] * fr;
+        cluster.sync();
+        // totals over the cluster, then the whole normalised y from the owners
+        float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+        for (int w = 0; w < 8; ++w) { c += pv[0][w]; d += pv[1][w]; }
+        for (int r = 0; r < CS; ++r) {
+            const float* pn = cluster.map_shared_rank(pnorm, r);
+            a += pn[0]; b += pn[1];
         }
-        __syncthreads();
+        ns = c > 0.f ? sqrtf(a / c) : 0.f;     // |B v| / |v|
+        nr = d > 0.f ? sqrtf(b / d) : 0.f;
+        const float fs = a > 0.f ? rsqrtf(a) : 0.f, fr = b > 0.f ? rsqrtf(b) : 0.f;
+        for (int i = threadIdx.x; i < Mp; i += 256) {
+            const int r = i / rows, q = i - r * rows;
+            vs[i] = cluster.map_shared_rank(ys, r)[q] * fs;
+            vr[i] = cluster.map_shared_rank(yr, r)[q] * fr;
+        }
+        // every CTA has read the chunks before they are overwritten
+        cluster.sync();
     }
-    if (threadIdx.x == 0) {
-        double lm = 0.0;
-        for (int w = 0; w < 16; ++w) lm = fmax(lm, lmax_sh[w]);
-        norms[mat] = 2.0 * 1.5 * ((double)ns + lm * (double)nr);
+    if (crank == 0 && threadIdx.x == 0) {
+        float lm = 0.f;
+        for (int r = 0; r < CS; ++r) lm = fmaxf(lm, cluster.map_shared_rank(pnorm, r)[2]);
+        norms[mat] = 2.0 * 1.5 * ((double)ns + (double)lm * (double)nr);
     }
+    // keep the shared memory alive until rank 0 has read it
+    cluster.sync();
 }
 
 // Rows of X back to unit length: the refinement keeps the rows orthogonal to
@@ -342,8 +365,26 @@ cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* 
             RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W2, Mp, st, 0, X, Mp, st, 1, 0.0, W3, Mp, st, s, 1));
         }
     }
-    k_oa_norms<<<nmat, 512, 0, s>>>(W1, W3, Mp, lam, norms);
-    RK_CUDA_TRY(cudaGetLastError());
+    {
+        // cluster size: enough CTAs to cover the GPU, a divisor of Mp, <= 16
+        int cs = 1;
+        while (cs < 16 && nmat * cs < 304 && Mp % (2 * cs) == 0) cs *= 2;
+        if (cs > 8)
+            RK_CUDA_TRY(cudaFuncSetAttribute(k_oa_norms, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nmat * cs), 1, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        RK_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_oa_norms, (const double*)W1, (const double*)W3, Mp, cs,
+                                       lam, norms));
+    }
     const int bx = (int)std::min<int64_t>(ceil_div(st, 256), 1024);
     k_oa_E<<<dim3(bx, nmat), 256, 0, s>>>(W1, W3, Mp, lam, norms);
     RK_CUDA_TRY(cudaGetLastError());
