@@ -115,7 +115,7 @@ struct svd_plan_s {
 
 namespace {
 
-constexpr int64_t kChunkCols = 16384;
+constexpr int64_t kChunkCols = 512;
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 

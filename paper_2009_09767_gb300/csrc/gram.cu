@@ -4,9 +4,9 @@
 // A column a_j adds the outer product a_j a_j^T, so a block's cross product
 // costs sum_j k_j (k_j + 1) / 2 multiply-adds over its columns of k_j
 // entries: the work that sparsity leaves, none of the dense M x w product.
-// One CTA streams a column chunk (all in one block); a warp owns a column and
-// scatters its upper-triangle products with FP64 atomic adds into the block's
-// M x M matrix (row-major, padded to Mp).
+// One CTA streams a column chunk (all in one block) and scatters the
+// upper-triangle products of its columns with FP64 atomic adds into the
+// block's M x M matrix (row-major, padded to Mp).
 #include <algorithm>
 
 #include "common.cuh"
@@ -14,17 +14,48 @@
 
 namespace rk {
 
+// Columns with up to kLight entries are taken by one thread each (their
+// k (k + 1) / 2 products issued back to back); longer ones are queued and
+// taken by a warp each, lanes over the second index.
+namespace {
+constexpr int kLight = 32;
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_gram(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
        const void* __restrict__ vals, int value_type, int Mp,
        const int32_t* __restrict__ chunk_block, const int64_t* __restrict__ chunk_col_lo,
        const int64_t* __restrict__ chunk_col_hi, double* __restrict__ G) {
+    __shared__ int64_t heavy[kThreads * 4];
+    __shared__ int nheavy;
     const int c = blockIdx.x;
     const int d = chunk_block[c];
     double* Gd = G + (int64_t)d * Mp * Mp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kWarps = kThreads / 32;
-    for (int64_t j = chunk_col_lo[c] + warp; j < chunk_col_hi[c]; j += kWarps) {
+    if (threadIdx.x == 0) nheavy = 0;
+    __syncthreads();
+    const int64_t lo = chunk_col_lo[c], hi = chunk_col_hi[c];
+    for (int64_t j = lo + threadIdx.x; j < hi; j += kThreads) {
+        const int64_t e0 = col_ptr[j], e1 = col_ptr[j + 1];
+        if (e1 - e0 > kLight) {
+            const int h = atomicAdd(&nheavy, 1);
+            if (h < kThreads * 4) { heavy[h] = j; continue; }
+        }
+        for (int64_t a = e0; a < e1; ++a) {
+            const double va = load_val(vals, value_type, a);
+            if (va == 0.0) continue;
+            double* row = Gd + (int64_t)row_idx[a] * Mp;
+            for (int64_t b = a; b < e1; ++b) {
+                const double vb = load_val(vals, value_type, b);
+                if (vb != 0.0) atomicAdd(row + row_idx[b], va * vb);
+            }
+        }
+    }
+    __syncthreads();
+    const int nh = min(nheavy, kThreads * 4);
+    for (int h = warp; h < nh; h += kWarps) {
+        const int64_t j = heavy[h];
         const int64_t e0 = col_ptr[j], e1 = col_ptr[j + 1];
         for (int64_t a = e0; a < e1; ++a) {
             const int ra = row_idx[a];

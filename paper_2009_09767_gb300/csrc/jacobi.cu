@@ -1028,11 +1028,12 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
                 float c = 1.f, sn = 0.f;
                 fp = -1;
                 if (fabsf(g) > floor_abs && g * g > tol2 * fabsf(a * d)) {
-                    const float zeta = (d - a) / (2.f * g);
-                    const float az = fabsf(zeta);
-                    float t = az < 1e18f ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f)))
-                                         : __frcp_rn(2.f * az);
-                    if (zeta < 0.f) t = -t;
+                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (d - a) / (2 g),
+                    // written without the division: t = sign(h g) 2|g| / (|h| + sqrt(h^2 + 4 g^2))
+                    const float h = d - a;
+                    const float rr = sqrtf(fmaf(h, h, 4.f * g * g));
+                    float t = 2.f * fabsf(g) * __frcp_rn(fabsf(h) + rr);
+                    if ((h < 0.f) != (g < 0.f)) t = -t;
                     const float x = fmaf(t, t, 1.f);
                     c = rsqrtf(x);
                     c = c * fmaf(-0.5f * x, c * c, 1.5f);

@@ -3,8 +3,8 @@
 //
 // Row j of V (k contiguous values) is the combination of the rows of
 // W = U_k S_k^-1 picked by column j's entries: V[j,:] = sum_e a_e W[row_e,:].
-// One warp owns a column; each lane holds a 16-byte slice of the output row,
-// so a warp writes 512 contiguous bytes per pass with streaming stores (V is
+// One warp owns a column; each lane holds 16-byte slices of the output row,
+// so a warp writes 512 contiguous bytes per store with streaming stores (V is
 // written once and never re-read).  W (M x k) stays in L2 / L1.  The kernel
 // is bound by the store of V: N * k * sizeof(T) bytes.
 #include <algorithm>
@@ -37,8 +37,12 @@ __device__ __forceinline__ T load_as(const void* vals, int64_t e) {
     return (T) static_cast<const VT*>(vals)[e];
 }
 
-// vector path: k % Vec<T>::n == 0
-template <typename T, typename VT>
+// vector path: k % Vec<T>::n == 0 and k / Vec<T>::n <= 32 CPL.  A warp
+// loads up to 32 of the column's entries at once (one per lane) and
+// broadcasts them; each lane accumulates its CPL slices of the output row in
+// one pass over the entries, so every W load of an entry issues together and
+// a column costs a few dependent memory trips, not one per slice.
+template <typename T, typename VT, int CPL>
 __global__ void __launch_bounds__(256)
 k_spmm_vec(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
            const void* __restrict__ vals, int64_t N, int k, const T* __restrict__ W,
@@ -51,18 +55,36 @@ k_spmm_vec(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_
     const int kv = k / NV;                 // vectors per row
     for (int64_t j = warp; j < N; j += nwarps) {
         const int64_t e0 = col_ptr[j], e1 = col_ptr[j + 1];
-        V4* out = reinterpret_cast<V4*>(V + j * (int64_t)k);
-        for (int c = lane; c < kv; c += 32) {
-            V4 acc;
-            if constexpr (NV == 4) acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            else acc = make_double2(0.0, 0.0);
-            for (int64_t e = e0; e < e1; ++e) {
-                const int r = __ldg(row_idx + e);
-                const T a = load_as<T, VT>(vals, e);
-                const V4 w = __ldg(reinterpret_cast<const V4*>(W + (int64_t)r * k) + c);
-                fma_vec<T>(acc, a, w);
+        V4 acc[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            if constexpr (NV == 4) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            else acc[q] = make_double2(0.0, 0.0);
+        }
+        for (int64_t eb = e0; eb < e1; eb += 32) {
+            const int n = (int)min((int64_t)32, e1 - eb);
+            int my_r = 0;
+            T my_a = T(0);
+            if (lane < n) {
+                my_r = __ldg(row_idx + eb + lane);
+                my_a = load_as<T, VT>(vals, eb + lane);
             }
-            __stcs(out + c, acc);
+            for (int i = 0; i < n; ++i) {
+                const int r = __shfl_sync(0xffffffffu, my_r, i);
+                const T a = __shfl_sync(0xffffffffu, my_a, i);
+                const V4* wr = reinterpret_cast<const V4*>(W + (int64_t)r * k);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < kv) fma_vec<T>(acc[q], a, __ldg(wr + c));
+                }
+            }
+        }
+        V4* out = reinterpret_cast<V4*>(V + j * (int64_t)k);
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int c = lane + 32 * q;
+            if (c < kv) __stcs(out + c, acc[q]);
         }
     }
 }
@@ -110,14 +132,17 @@ cudaError_t launch_spmm(const int64_t* col_ptr, const int32_t* row_idx, const vo
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = ceil_div(N * 32, 256);
     const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 16);
-    const bool vec = (k % Vec<T>::n) == 0;
-    if (value_type == 0) {
-        if (vec) k_spmm_vec<T, float><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
-        else k_spmm_scalar<T, float><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
-    } else {
-        if (vec) k_spmm_vec<T, double><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
-        else k_spmm_scalar<T, double><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
-    }
+    const int kv = (k % Vec<T>::n) == 0 ? k / Vec<T>::n : -1;
+    auto go = [&](auto vt_tag) {
+        using VT = decltype(vt_tag);
+        if (kv > 0 && kv <= 32) k_spmm_vec<T, VT, 1><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
+        else if (kv > 0 && kv <= 64) k_spmm_vec<T, VT, 2><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
+        else if (kv > 0 && kv <= 128) k_spmm_vec<T, VT, 4><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
+        else if (kv > 0 && kv <= 256) k_spmm_vec<T, VT, 8><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
+        else k_spmm_scalar<T, VT><<<grid, 256, 0, s>>>(col_ptr, row_idx, vals, N, k, W, V);
+    };
+    if (value_type == 0) go(float{});
+    else go(double{});
     return cudaGetLastError();
 }
 
