@@ -117,12 +117,16 @@ def source_hash(rel: str) -> str:
 
 
 def jacobi_flops(sweeps: np.ndarray, Mp: int) -> float:
-    """Algorithmic FP32 flops of the block Jacobi launch: per sweep and matrix,
-    the three panel products (rows of G, columns of G, rows of the eigenvector
-    matrix) cost 6 Mp^3 multiply-adds in total, and the 64 x 64 sub-problem
-    sweeps 8 * 64 * Mp^2 multiply-adds."""
-    per_sweep = 2.0 * (6.0 * Mp ** 3 + 8.0 * 64 * Mp ** 2)
-    return float(np.sum(np.abs(sweeps))) * per_sweep
+    """Algorithmic FP32 flops of the block Jacobi launch.  A sweep has
+    Mp/16 - 1 steps; a step with np = Mp/32 pairs updates the np (np + 1) / 2
+    symmetric 32 x 32 blocks of G (two 32^3 products each), the eigenvector
+    columns (np * Mp/32 products of 32^3) and solves np 32 x 32 sub-problems
+    (31 rounds x 16 rotations, each rotation 6 flops on 3 x 2 x 32 values)."""
+    n_p = Mp // 32
+    steps = Mp // 16 - 1
+    per_step = (n_p * (n_p + 1) / 2 * 2 * 2 * 32 ** 3 + n_p * (Mp // 32) * 2 * 32 ** 3
+                + n_p * 31 * 16 * 6 * 3 * 32)
+    return float(np.sum(np.abs(sweeps))) * steps * per_step
 
 
 def algorithmic_bytes(case, R: int, k: int, s_v: int) -> float:
@@ -532,7 +536,7 @@ def main():
     jac_ms = stage_ms["block_jacobi"]
     jac_flops = jacobi_flops(sweeps[:-1], Mp)
     achieved = jac_flops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else 0.0
-    roofline = {"kernel": f"k_jacobi<float,64> ({case.num_blocks} blocks of 512 x 512)",
+    roofline = {"kernel": f"k_jacobi4 ({case.num_blocks} blocks of 512 x 512)",
                 "bound": "alu",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
@@ -550,6 +554,20 @@ def main():
            "peak_gbs": (peaks or {}).get("hbm_gbs", 6800.0),
            "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback 6.8 TB/s"}
     hbm["frac"] = hbm["gbs"] / hbm["peak_gbs"]
+    # HBM rooflines of the memory-side stages (stage events on the launch stream):
+    # the SpMM writes V once and reads the CSC and W; the cross-product stage reads
+    # the CSC and writes the FP64 cross products and their FP32 copy
+    csc_bytes = case.col_ptr.nbytes + case.row_idx.nbytes + case.vals.nbytes
+    v_bytes = case.N * plan.k * s_v
+    g_bytes = case.num_blocks * Mp * Mp * (8 + (4 if args.precision == "mixed" else 8))
+    hbm_kernels = {}
+    for name, stage, nbytes in (("spmm (k_spmm_vec)", "spmm", v_bytes + csc_bytes + case.M * plan.k * s_v),
+                                ("cross products (k_gram, k_symmetrize, k_convert)", "gram",
+                                 g_bytes + csc_bytes)):
+        ms_k = stage_ms[stage]
+        gbs = nbytes / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0
+        hbm_kernels[name] = {"algorithmic_bytes": float(nbytes), "ms": ms_k, "gbs": gbs,
+                             "frac": gbs / hbm["peak_gbs"]}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -579,7 +597,7 @@ def main():
                              "workspace, far above the 129 MB L2"},
             "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches * args.steps, "launches_per_step": launches,
-            "clocks": clock_info, "stage_ms": stage_ms,
+            "clocks": clock_info, "stage_ms": stage_ms, "hbm_kernels": hbm_kernels,
             "sweeps": {"blocks_min": int(np.abs(sweeps[:-1]).min()),
                        "blocks_max": int(np.abs(sweeps[:-1]).max()), "merge": int(sweeps[-1])},
             "rank": rank_out, "proxy_cols": R,

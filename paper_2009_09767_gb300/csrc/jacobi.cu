@@ -993,8 +993,8 @@ __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restr
 // (named barrier bar, 32 K threads), accumulating Q.  Warp 0 of the group
 // computes the round's 16 rotations (lanes 0..15) and, at the start of the
 // next round, writes the exact 2 x 2 diagonal blocks of the rotated pairs;
-// the row pass and the column pass (sub and Q) are split over the K warps
-// by pair.  The rotation parameters use the fast reciprocal and square root
+// the two-sided update of the 256 2 x 2 blocks and the column pass of Q are
+// split over the K warps (two barriers per round).  The rotation parameters use the fast reciprocal and square root
 // (the angle only steers convergence); c is polished by one Newton step so
 // that c^2 + s^2 = 1 to about an ulp (orthogonality of Q).
 __device__ __forceinline__ void group_bar(int id, int nthreads) {
@@ -1057,26 +1057,24 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
         group_bar(bar, 32 * K);
         if (!act[r & 1]) continue;   // uniform over the group
         any_round = true;
-        // rows p, q (lane = column)
+        // two-sided update, one 2 x 2 block (rows p_u, q_u; columns p_w, q_w)
+        // per thread: R_u^T S R_w, so no ordering between a row and a column
+        // pass is needed; then columns p_w, q_w of Q (lane = row)
 #pragma unroll
-        for (int h = 0; h < NU; h += HB) {
-            float cu[HB], su[HB], x[HB], y[HB];
-            int pu[HB], qu[HB];
-#pragma unroll
-            for (int v = 0; v < HB; ++v) {
-                const int u = wi + (h + v) * K;
-                cu[v] = rc[u]; su[v] = rs[u]; pu[v] = rp[u]; qu[v] = rq[u];
-            }
-#pragma unroll
-            for (int v = 0; v < HB; ++v) { x[v] = sub[pu[v] * LD + lane]; y[v] = sub[qu[v] * LD + lane]; }
-#pragma unroll
-            for (int v = 0; v < HB; ++v) {
-                sub[pu[v] * LD + lane] = cu[v] * x[v] - su[v] * y[v];
-                sub[qu[v] * LD + lane] = su[v] * x[v] + cu[v] * y[v];
-            }
+        for (int i = 0; i < 256 / (32 * K); ++i) {
+            const int b = (wi + K * i) * 32 + lane;
+            const int u = b >> 4, w = b & 15;
+            const float cu = rc[u], su = rs[u], cw = rc[w], sw = rs[w];
+            const int pu = rp[u], qu = rq[u], pw = rp[w], qw = rq[w];
+            const float x11 = sub[pu * LD + pw], x12 = sub[pu * LD + qw];
+            const float x21 = sub[qu * LD + pw], x22 = sub[qu * LD + qw];
+            const float y11 = cu * x11 - su * x21, y21 = su * x11 + cu * x21;
+            const float y12 = cu * x12 - su * x22, y22 = su * x12 + cu * x22;
+            sub[pu * LD + pw] = cw * y11 - sw * y12;
+            sub[pu * LD + qw] = sw * y11 + cw * y12;
+            sub[qu * LD + pw] = cw * y21 - sw * y22;
+            sub[qu * LD + qw] = sw * y21 + cw * y22;
         }
-        group_bar(bar, 32 * K);
-        // columns p, q of sub and of Q (lane = row)
 #pragma unroll
         for (int h = 0; h < NU; h += HB) {
             float cu[HB], su[HB], x[HB], y[HB];
@@ -1085,13 +1083,6 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
             for (int v = 0; v < HB; ++v) {
                 const int u = wi + (h + v) * K;
                 cu[v] = rc[u]; su[v] = rs[u]; pu[v] = rp[u]; qu[v] = rq[u];
-            }
-#pragma unroll
-            for (int v = 0; v < HB; ++v) { x[v] = sub[lane * LD + pu[v]]; y[v] = sub[lane * LD + qu[v]]; }
-#pragma unroll
-            for (int v = 0; v < HB; ++v) {
-                sub[lane * LD + pu[v]] = cu[v] * x[v] - su[v] * y[v];
-                sub[lane * LD + qu[v]] = su[v] * x[v] + cu[v] * y[v];
             }
 #pragma unroll
             for (int v = 0; v < HB; ++v) { x[v] = Q[lane * LD + pu[v]]; y[v] = Q[lane * LD + qu[v]]; }
