@@ -823,6 +823,12 @@ __device__ __forceinline__ void mma_split(float (&d)[4], const uint32_t (&ah)[4]
 }
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t* p) { return __ldcg(p); }
+// rotation words from the CTA's shared copy (kS) or from L2
+template <bool kS>
+__device__ __forceinline__ uint32_t ldq(const uint32_t* p) {
+    if constexpr (kS) return *p;
+    else return __ldcg(p);
+}
 __device__ __forceinline__ float2 ldcg_f2(const float* p) {
     return __ldcg(reinterpret_cast<const float2*>(p));
 }
@@ -836,6 +842,7 @@ __device__ __forceinline__ float2 ldcg_f2(const float* p) {
 // first product is read through the symmetry, B[k][n] = G[P_w(n)][P_u(k)],
 // so every fragment is a consecutive pair.  On the diagonal (u == w) only the
 // upper triangle is written, to both halves.
+template <bool kS>
 __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restrict__ Qu,
                           const uint32_t* __restrict__ Qw, int ui, int uj, int wi, int wj) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -854,14 +861,14 @@ __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restr
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi) {
             const int m = mi * 16 + g, kp = kk * 8 + t;
-            ah[mi][0] = ldcg_u32(Qu + m * 16 + kp);
-            ah[mi][1] = ldcg_u32(Qu + (m + 8) * 16 + kp);
-            ah[mi][2] = ldcg_u32(Qu + m * 16 + kp + 4);
-            ah[mi][3] = ldcg_u32(Qu + (m + 8) * 16 + kp + 4);
-            al[mi][0] = ldcg_u32(Qu + kQWords + m * 16 + kp);
-            al[mi][1] = ldcg_u32(Qu + kQWords + (m + 8) * 16 + kp);
-            al[mi][2] = ldcg_u32(Qu + kQWords + m * 16 + kp + 4);
-            al[mi][3] = ldcg_u32(Qu + kQWords + (m + 8) * 16 + kp + 4);
+            ah[mi][0] = ldq<kS>(Qu + m * 16 + kp);
+            ah[mi][1] = ldq<kS>(Qu + (m + 8) * 16 + kp);
+            ah[mi][2] = ldq<kS>(Qu + m * 16 + kp + 4);
+            ah[mi][3] = ldq<kS>(Qu + (m + 8) * 16 + kp + 4);
+            al[mi][0] = ldq<kS>(Qu + kQWords + m * 16 + kp);
+            al[mi][1] = ldq<kS>(Qu + kQWords + (m + 8) * 16 + kp);
+            al[mi][2] = ldq<kS>(Qu + kQWords + m * 16 + kp + 4);
+            al[mi][3] = ldq<kS>(Qu + kQWords + (m + 8) * 16 + kp + 4);
         }
         const int k = kk * 16 + 2 * t;
         const int c0 = gidx(ui, uj, k), c1 = gidx(ui, uj, k + 8);
@@ -900,9 +907,9 @@ __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restr
 #pragma unroll
         for (int nj = 0; nj < 4; ++nj) {
             const int n = nj * 8 + g, kp = kk * 8 + t;
-            const uint32_t bh0 = ldcg_u32(Qw + n * 16 + kp), bh1 = ldcg_u32(Qw + n * 16 + kp + 4);
-            const uint32_t bl0 = ldcg_u32(Qw + kQWords + n * 16 + kp);
-            const uint32_t bl1 = ldcg_u32(Qw + kQWords + n * 16 + kp + 4);
+            const uint32_t bh0 = ldq<kS>(Qw + n * 16 + kp), bh1 = ldq<kS>(Qw + n * 16 + kp + 4);
+            const uint32_t bl0 = ldq<kS>(Qw + kQWords + n * 16 + kp);
+            const uint32_t bl1 = ldq<kS>(Qw + kQWords + n * 16 + kp + 4);
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi) mma_split(out[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
         }
@@ -938,6 +945,7 @@ __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restr
 }
 
 // Column job: V[r0..r0+31, P_u] <- V[r0..r0+31, P_u] Q_u.
+template <bool kS>
 __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restrict__ Qu, int ui,
                           int uj, int r0) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -967,9 +975,9 @@ __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restr
 #pragma unroll
         for (int nj = 0; nj < 4; ++nj) {
             const int n = nj * 8 + g, kp = kk * 8 + t;
-            const uint32_t bh0 = ldcg_u32(Qu + n * 16 + kp), bh1 = ldcg_u32(Qu + n * 16 + kp + 4);
-            const uint32_t bl0 = ldcg_u32(Qu + kQWords + n * 16 + kp);
-            const uint32_t bl1 = ldcg_u32(Qu + kQWords + n * 16 + kp + 4);
+            const uint32_t bh0 = ldq<kS>(Qu + n * 16 + kp), bh1 = ldq<kS>(Qu + n * 16 + kp + 4);
+            const uint32_t bl0 = ldq<kS>(Qu + kQWords + n * 16 + kp);
+            const uint32_t bl1 = ldq<kS>(Qu + kQWords + n * 16 + kp + 4);
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi) mma_split(out[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
         }
@@ -1190,6 +1198,7 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     const int kgrp = nmine >= kW4 ? 1 : nmine >= 4 ? 2 : nmine >= 2 ? 4 : 8;
     const int ngroups = kW4 / kgrp, grp = warp / kgrp, wi = warp % kgrp;
     int* ident = reinterpret_cast<int*>(qbuf + (size_t)np * 2 * kQWords);   // np flags
+    const bool qsmem = ((size_t)np * 2 * kQWords + np) * sizeof(uint32_t) <= J4Smem::bytes;
     const int nblk = np * (np + 1) / 2;
     const int rtiles = Mp / kB2;
     const int njobs = nblk + np * rtiles;
@@ -1217,6 +1226,20 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                 }
             }
             owner_sync<kCluster>();
+            // the step's rotations and identity flags into this CTA's shared
+            // memory (the solve area is free now) when they fit
+            const uint32_t* qsrc = qbuf;
+            const int* isrc = ident;
+            if (qsmem) {
+                uint32_t* qs = reinterpret_cast<uint32_t*>(smem_raw);
+                const int nw = np * 2 * kQWords;
+                for (int w = threadIdx.x; w < nw / 4; w += kJT4)
+                    reinterpret_cast<uint4*>(qs)[w] = __ldcg(reinterpret_cast<const uint4*>(qbuf) + w);
+                for (int w = threadIdx.x; w < np; w += kJT4) qs[nw + w] = (uint32_t)__ldcg(ident + w);
+                __syncthreads();
+                qsrc = qs;
+                isrc = reinterpret_cast<const int*>(qs + nw);
+            }
             for (int j = gwarp; j < njobs; j += nwarps) {
                 int u, w2 = 0;
                 if (j < nblk) {
@@ -1225,21 +1248,32 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                     while (r >= np - u) { r -= np - u; ++u; }
                     w2 = u + r;
                     // both rotations the identity: the block does not change
-                    if (__ldcg(ident + u) && __ldcg(ident + w2)) continue;
+                    const bool id_u = qsmem ? isrc[u] != 0 : __ldcg(ident + u) != 0;
+                    const bool id_w = qsmem ? isrc[w2] != 0 : __ldcg(ident + w2) != 0;
+                    if (id_u && id_w) continue;
                     int ui, uj, wi2, wj;
                     circle_pair(nb, step, u, ui, uj);
                     circle_pair(nb, step, w2, wi2, wj);
-                    job_block(G, Mp, qbuf + (size_t)u * 2 * kQWords, qbuf + (size_t)w2 * 2 * kQWords,
-                              ui, uj, wi2, wj);
+                    if (qsmem)
+                        job_block<true>(G, Mp, qsrc + (size_t)u * 2 * kQWords, qsrc + (size_t)w2 * 2 * kQWords,
+                                        ui, uj, wi2, wj);
+                    else
+                        job_block<false>(G, Mp, qsrc + (size_t)u * 2 * kQWords, qsrc + (size_t)w2 * 2 * kQWords,
+                                         ui, uj, wi2, wj);
                 } else {
                     const int r = j - nblk;
                     u = r / rtiles;
-                    if (__ldcg(ident + u)) continue;
+                    if (qsmem ? isrc[u] != 0 : __ldcg(ident + u) != 0) continue;
                     int ui, uj;
                     circle_pair(nb, step, u, ui, uj);
-                    job_vcols(V, Mp, qbuf + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
+                    if (qsmem)
+                        job_vcols<true>(V, Mp, qsrc + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
+                    else
+                        job_vcols<false>(V, Mp, qsrc + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
                 }
             }
+            // (the next step's solves overwrite the shared copy: every warp of
+            // this CTA has finished its jobs at the barrier below)
             owner_sync<kCluster>();
         }
         ++sweep;
