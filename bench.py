@@ -48,6 +48,23 @@ def dist_env():
     return ws, rank, local
 
 
+def slowest(local_value: float, ws: int, device=None) -> float:
+    """The largest value over the ranks (the slowest rank's time); the local
+    value when there is one rank."""
+    if ws <= 1:
+        return float(local_value)
+    import torch
+    t = torch.tensor([float(local_value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank processes the same number)."""
+    return ws * units_per_rank / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -305,7 +322,8 @@ def run_serve(args):
     out = {"metric": "serving p50/p99 latency and throughput", "unit": "ms", "data": "synthetic",
            "config": {"workload": "Poisson arrivals, 95% batch_mix-shaped, 5% zipf_wide-shaped "
                                   "(512 x 1e6), V copied back", "budget_bytes": 40 << 30,
-                      "max_inflight": 16, "duration_s_per_rate": args.duration},
+                      "max_inflight": 16, "duration_s_per_rate": args.duration,
+                      "grace_s": args.grace},
            "rates": []}
     pinned = {}
 
@@ -337,10 +355,21 @@ def run_serve(args):
                 o = outputs_for(c, prec, slot)
                 tickets.append(srv.submit(c.M, c.N, c.col_ptr, c.row_idx, c.vals, c.num_blocks, o,
                                           precision=prec))
-            lat, fails, last_done = [], 0, 0.0
+            # requests still queued a grace period after the last arrival are
+            # cancelled and counted as dropped (an overloaded server would
+            # otherwise drain its backlog for minutes); admitted ones finish
+            deadline = t_start + args.duration + args.grace
+            lat, fails, dropped, last_done = [], 0, 0, 0.0
             first = None
             for t in tickets:
-                st = srv.wait(t, timeout=600.0)
+                call, st = srv.wait_status(t, max(0.0, deadline - time.perf_counter()))
+                if call == 7:      # SVD_ERR_TIMEOUT: not finished by the deadline
+                    if srv.cancel(t) == 0:
+                        srv.wait_status(t, 60.0)
+                        dropped += 1
+                        srv.release(t)
+                        continue
+                    st = srv.wait(t, timeout=600.0)
                 ts, ta, td = srv.times(t)
                 first = ts if first is None else min(first, ts)
                 last_done = max(last_done, td)
@@ -353,6 +382,7 @@ def run_serve(args):
             srv.close()
             out["rates"].append({
                 "precision": prec, "rate_req_s": rate, "requests": n, "failed": fails,
+                "dropped_after_grace": dropped,
                 "completed_per_s": len(lat) / max(last_done - first, 1e-9),
                 "p50_ms": float(np.percentile(lat, 50)) if lat else None,
                 "p99_ms": float(np.percentile(lat, 99)) if lat else None,
@@ -425,6 +455,8 @@ def main():
     ap.add_argument("--count", type=int, default=2000, help="batch: matrices")
     ap.add_argument("--rates", default="50,100,200,400", help="serve: arrival rates (req/s)")
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds per rate")
+    ap.add_argument("--grace", type=float, default=15.0,
+                    help="serve: seconds after the last arrival before queued requests are dropped")
     ap.add_argument("--large-cols", type=int, default=8_000_000, help="large: columns")
     args = ap.parse_args()
 
@@ -487,11 +519,7 @@ def main():
         torch.distributed.barrier()
     clock_info = clocks.stop() if clocks else None
     plan.sync()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = slowest(ev0.elapsed_time(ev1), ws, dev)
     totals = plan.query(rk.Q_STAGE_TOTAL)
     stage_ms = {n: float(totals[i] / max(totals[-1], 1)) for i, n in enumerate(rk.STAGES)}
     launches = int(plan.query(rk.Q_LAUNCHES)[0])
@@ -499,7 +527,7 @@ def main():
     R = int(plan.query(rk.Q_PROXY_COLS)[0])
     rank_out = int(out["rank"].item())
     ms_per_step = elapsed_ms / args.steps
-    value = ws * args.steps / (elapsed_ms / 1e3)
+    value = job_rate(args.steps, ws, elapsed_ms / 1e3)
 
     # end to end through the host-buffer entry point: H2D of the CSC, D2H of
     # sigma, U, V and rank inside the timed region
@@ -521,14 +549,10 @@ def main():
         n_e2e = max(3, args.steps // 2)
         for _ in range(n_e2e):
             plan.run_host(h_cp, h_ri, h_va, h_s, h_U, h_V, h_r, stream=stream)
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = slowest(time.perf_counter() - t0, ws, dev)
         h2d = case.col_ptr.nbytes + case.row_idx.nbytes + case.vals.nbytes
         d2h = h_s.numel() * 8 + h_U.numel() * 8 + h_V.numel() * h_V.element_size() + 4
-        e2e = {"value": ws * n_e2e / dt, "unit": "SVD/s", "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": job_rate(n_e2e, ws, dt), "unit": "SVD/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
 
     # roofline of the dominant kernel (block Jacobi, FP32 ALU-bound)
@@ -536,7 +560,8 @@ def main():
     jac_ms = stage_ms["block_jacobi"]
     jac_flops = jacobi_flops(sweeps[:-1], Mp)
     achieved = jac_flops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else 0.0
-    roofline = {"kernel": f"k_jacobi4 ({case.num_blocks} blocks of 512 x 512)",
+    jac_kernel = "k_jacobi4" if args.precision == "mixed" else "k_jacobi<double>"
+    roofline = {"kernel": f"{jac_kernel} ({case.num_blocks} blocks of 512 x 512)",
                 "bound": "alu",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
