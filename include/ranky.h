@@ -154,7 +154,9 @@ svd_status svd_run(svd_plan_t plan, const int64_t* d_col_ptr, const int32_t* d_r
 /* Same computation from HOST buffers: copies the CSC to plan-owned device
  * memory, runs, and copies sigma, U, V (unless SVD_FLAG_SKIP_V or h_V ==
  * NULL), rank and patches back.  Synchronous; pinned host memory makes the
- * copies fast but is not required. */
+ * copies fast but is not required.  When h_V is page-locked (cudaHostAlloc,
+ * cudaHostRegister) and the rank fix is TRUNCATE, the device writes V into
+ * it directly, with no staging buffer and no copy. */
 svd_status svd_run_host(svd_plan_t plan, const int64_t* h_col_ptr, const int32_t* h_row_idx,
                         const void* h_vals, double* h_sigma, double* h_U, void* h_V,
                         int32_t* h_rank, svd_patch* h_patches, int64_t* h_npatches,

@@ -653,13 +653,26 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
     const size_t sv = p->d.value_type == SVD_VALUE_F32 ? 4 : 8;
     const size_t sV = p->mixed ? 4 : 8;
     const bool want_v = h_V && !(p->d.flags & SVD_FLAG_SKIP_V);
+    // A page-locked V buffer is addressable from the device (unified
+    // addressing; on this part over the chip-to-chip link): the SpMM then
+    // streams V straight into it and the 2 GB copy disappears.  Not with
+    // RandomChecker insertions, whose V correction uses atomic adds.
+    void* dV_direct = nullptr;
+    if (want_v && !p->random) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, h_V) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer)
+            dV_direct = at.devicePointer;
+        cudaGetLastError();
+    }
+    const bool copy_v = want_v && !dV_direct;
     Carver dry{nullptr, 0, true};
     dry.take<int64_t>(p->N + 1);
     dry.take<int32_t>(std::max<int64_t>(p->nnz, 1));
     dry.take<char>(std::max<int64_t>(p->nnz, 1) * sv);
     dry.take<double>(p->k);
     dry.take<double>((size_t)p->M * p->k);
-    dry.take<char>(want_v ? (size_t)p->N * p->k * sV : 1);
+    dry.take<char>(copy_v ? (size_t)p->N * p->k * sV : 1);
     dry.take<int32_t>(1);
     dry.take<svd_patch>((size_t)p->D * p->M);
     dry.take<int64_t>(1);
@@ -679,7 +692,8 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
     char* va = c.take<char>(std::max<int64_t>(p->nnz, 1) * sv);
     double* sg = c.take<double>(p->k);
     double* U = c.take<double>((size_t)p->M * p->k);
-    char* V = c.take<char>(want_v ? (size_t)p->N * p->k * sV : 1);
+    char* V = copy_v ? c.take<char>((size_t)p->N * p->k * sV) : static_cast<char*>(dV_direct);
+    if (copy_v == false) c.take<char>(1);
     int32_t* rk_ = c.take<int32_t>(1);
     svd_patch* pt = c.take<svd_patch>((size_t)p->D * p->M);
     int64_t* np = c.take<int64_t>(1);
@@ -696,7 +710,7 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
     CU(cudaMemcpyAsync(h_sigma, sg, sizeof(double) * p->k, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h_U, U, sizeof(double) * p->M * p->k, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h_rank, rk_, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    if (want_v) CU(cudaMemcpyAsync(h_V, V, (size_t)p->N * p->k * sV, cudaMemcpyDeviceToHost, s));
+    if (copy_v) CU(cudaMemcpyAsync(h_V, V, (size_t)p->N * p->k * sV, cudaMemcpyDeviceToHost, s));
     if (h_npatches) CU(cudaMemcpyAsync(h_npatches, np, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (h_patches)
         CU(cudaMemcpyAsync(h_patches, pt, sizeof(svd_patch) * (size_t)p->D * p->M,

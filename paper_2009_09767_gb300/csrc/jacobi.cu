@@ -1,30 +1,35 @@
-// jacobi.cu -- batched block two-sided Jacobi eigensolver for the symmetric
+// jacobi.cu -- batched block two-sided Jacobi eigensolvers for the symmetric
 // positive semi-definite cross products of Ranky's block SVD (arXiv
 // 2009.09767, Eq. 1: A^i = U^i S^i V^i*, whose U^i and (S^i)^2 are the
 // eigenvectors and eigenvalues of A^i A^i^T).
 //
-// Design:
+// Common structure:
 //   * The index set 0..Mp-1 (Mp a multiple of 32) is cut into nb = Mp/16
 //     blocks of 16 indices.  A round-robin (circle) schedule pairs the blocks;
 //     each of the nb-1 steps of a sweep handles nb/2 disjoint block pairs.
-//   * A matrix is owned by a cluster of csize CTAs (512 threads); a CTA owns
-//     ppc = ceil(pairs / csize) pairs per step.  Each pair's 32 x 32
-//     sub-problem G[I+J, I+J] is solved by ONE WARP in shared memory: one
-//     cyclic sweep of 31 rounds x 16 disjoint rotations, synchronised with
-//     __syncwarp only, accumulating the 32 x 32 rotation Q.  Up to 16 pairs
-//     are solved at once by the CTA's 16 warps.
-//   * Phase A: rows I+J of G and of Vt become Q^T times themselves (panel
-//     products through shared memory, all 512 threads).  Cluster barrier.
-//     Phase B: columns I+J of G become themselves times Q.  Cluster barrier.
-//   * A sweep in which no rotation passed the threshold ends the solve.
-// G and Vt live in global memory (L2-resident at these sizes) and are read
-// with L2-only loads, because other CTAs of the cluster write them between
-// barriers.  Padding indices (M..Mp-1) hold zero rows and columns: they never
-// rotate, so their eigenvectors stay exact unit vectors.
+//   * A matrix is owned by a cluster of csize CTAs.  Each pair's 32 x 32
+//     sub-problem G[I+J, I+J] gets one cyclic sweep of 31 rounds x 16
+//     disjoint rotations in shared memory, accumulating its rotation Q; the
+//     step's rotation diag(Q_1, ..) is then applied to G and to the
+//     eigenvectors.  A sweep in which no rotation passed the threshold ends
+//     the solve.
+//   * G and the eigenvectors live in global memory (L2-resident at these
+//     sizes) and are read with L2-only loads, because other CTAs of the
+//     cluster write them between barriers.  Padding indices (M..Mp-1) hold
+//     zero rows and columns: they never rotate, so their eigenvectors stay
+//     exact unit vectors.
 //
-// Two launch forms: k_jacobi (one cluster per matrix, all matrices of one
-// size) and k_jacobi_items (persistent single-CTA workers that take matrices
-// of any size from a work list; used to batch many problems in one launch).
+// FP64 solver (k_jacobi<double>, k_jacobi_items<double>): one warp per pair
+// solve; phase A: rows I+J of G and of Vt become Q^T times themselves (panel
+// products through shared memory on the FP64 pipes), cluster barrier;
+// phase B: columns I+J of G become themselves times Q, cluster barrier.
+//
+// FP32 solver (k_jacobi4, k_jacobi4_items): see the section below; the
+// update runs as independent warp jobs on the tensor cores.
+//
+// Two launch forms each: one cluster per matrix (all matrices of one size),
+// and persistent single-CTA workers that take matrices of any size from a
+// work list (to batch many problems in one launch).
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
@@ -45,7 +50,7 @@ constexpr int kB2 = 32;           // sub-problem size
 constexpr int kB = kB2 / 2;       // index block size
 constexpr int kMaxCluster = 16;
 
-template <typename T> struct PairsMax { static constexpr int value = 16; };
+template <typename T> struct PairsMax;
 template <> struct PairsMax<double> { static constexpr int value = 8; };
 
 // circle schedule over n (even) items: partner pair u of round r
@@ -63,19 +68,12 @@ __device__ __forceinline__ void circle_pair(int n, int r, int u, int& a, int& b)
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
 template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
-template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
 template <typename T> struct V16;
-template <> struct V16<float> {
-    using type = float4;
-    static constexpr int n = 4;
-    __device__ static float get(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-};
 template <> struct V16<double> {
     using type = double2;
     static constexpr int n = 2;
@@ -119,8 +117,7 @@ struct JSmem {
     static constexpr int TR = 8192 / kB2;              // column-panel tile height (256)
     static constexpr int CSLD = kB2 + 4;
     static constexpr int STAGE = (kB2 * RSLD > TR * CSLD) ? kB2 * RSLD : TR * CSLD;
-    // FP32 panel tiles stream through two stage buffers (cp.async pipeline)
-    static constexpr int NSTAGE = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int NSTAGE = 1;
     static constexpr size_t bytes(int ppc) {
         return sizeof(T) * ((size_t)NSTAGE * STAGE + 2ull * ppc * kB2 * LD + 2ull * ppc * kB) +
                sizeof(int) * 2ull * ppc * kB;
@@ -222,129 +219,6 @@ __device__ __forceinline__ int gidx(int bi, int bj, int k) {
     return k < kB ? bi * kB + k : bj * kB + (k - kB);
 }
 
-// ---------------------------------------------------------------------------
-// FP32 panel products on the tensor cores: mma.sync m16n8k8 with TF32
-// operands, each FP32 value split as hi = tf32(x), lo = tf32(x - hi) and the
-// product accumulated as lo*hi + hi*lo + hi*hi in FP32 ("3xTF32"), which keeps
-// the rounding of an FP32 product (the lo*lo term is below it).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// d += A * B for one 16 x 8 x 8 step from FP32 fragments, 3xTF32.
-__device__ __forceinline__ void mma3(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
-    uint32_t ah[4], al[4], bh[2], bl[2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
-#pragma unroll
-    for (int i = 0; i < 2; ++i) split_tf32(b[i], bh[i], bl[i]);
-    mma_tf32(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
-}
-
-// Row panel tile on the tensor cores: out (32 x TW) = Q^T (32 x 32) * X (32 x TW)
-// with X = stage.  Warp w owns n-tiles 2w, 2w+1 (16 columns) and both m-tiles.
-// Fragment coordinates (m16n8k8): g = lane / 4, t = lane % 4;
-//   A: (g, t) (g+8, t) (g, t+4) (g+8, t+4);  B: (k=t, n=g) (k=t+4, n=g);
-//   C: (g, 2t) (g, 2t+1) (g+8, 2t) (g+8, 2t+1).
-__device__ __forceinline__ void tile_rows_tc(float* Mat, int Mp, int bi, int bj, int c0, int cw,
-                                             const float* Q, const float* stage) {
-    constexpr int LD = JSmem<float>::LD, SLD = JSmem<float>::RSLD;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][2][4] = {};
-#pragma unroll
-    for (int k0 = 0; k0 < kB2; k0 += 8) {
-        float a[2][4], b[2][2];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {            // A[m][k] = Q[k][m]
-            const int m = mt * 16 + g;
-            a[mt][0] = Q[(k0 + t) * LD + m];
-            a[mt][1] = Q[(k0 + t) * LD + m + 8];
-            a[mt][2] = Q[(k0 + t + 4) * LD + m];
-            a[mt][3] = Q[(k0 + t + 4) * LD + m + 8];
-        }
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {            // B[k][n] = stage[k][n]
-            const int n = (2 * warp + nt) * 8 + g;
-            b[nt][0] = stage[(k0 + t) * SLD + n];
-            b[nt][1] = stage[(k0 + t + 4) * SLD + n];
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) mma3(acc[mt][nt], a[mt], b[nt]);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-        const int n = (2 * warp + nt) * 8 + 2 * t;
-        if (n >= cw) continue;
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int m = mt * 16 + g;
-            *reinterpret_cast<float2*>(Mat + (int64_t)gidx(bi, bj, m) * Mp + c0 + n) =
-                make_float2(acc[mt][nt][0], acc[mt][nt][1]);
-            *reinterpret_cast<float2*>(Mat + (int64_t)gidx(bi, bj, m + 8) * Mp + c0 + n) =
-                make_float2(acc[mt][nt][2], acc[mt][nt][3]);
-        }
-    }
-}
-
-// Column panel tile on the tensor cores: out (TR x 32) = X (TR x 32) * Q (32 x 32)
-// with X = stage (row-major, stride CSLD).  Warp w owns m-tile w (16 rows), all
-// four n-tiles.
-__device__ __forceinline__ void tile_cols_tc(float* Mat, int Mp, int bi, int bj, int r0, int rh,
-                                             const float* Q, const float* stage) {
-    constexpr int LD = JSmem<float>::LD, SLD = JSmem<float>::CSLD;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[4][4] = {};
-    const int m = warp * 16 + g;
-#pragma unroll
-    for (int k0 = 0; k0 < kB2; k0 += 8) {
-        float a[4], b[4][2];
-        a[0] = stage[m * SLD + k0 + t];
-        a[1] = stage[(m + 8) * SLD + k0 + t];
-        a[2] = stage[m * SLD + k0 + t + 4];
-        a[3] = stage[(m + 8) * SLD + k0 + t + 4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            b[nt][0] = Q[(k0 + t) * LD + nt * 8 + g];
-            b[nt][1] = Q[(k0 + t + 4) * LD + nt * 8 + g];
-        }
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma3(acc[nt], a, b[nt]);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int n = nt * 8 + 2 * t;
-        const int gc = gidx(bi, bj, n);   // n, n+1 lie in the same half (n even)
-        if (m < rh)
-            *reinterpret_cast<float2*>(Mat + (int64_t)(r0 + m) * Mp + gc) =
-                make_float2(acc[nt][0], acc[nt][1]);
-        if (m + 8 < rh)
-            *reinterpret_cast<float2*>(Mat + (int64_t)(r0 + m + 8) * Mp + gc) =
-                make_float2(acc[nt][2], acc[nt][3]);
-    }
-}
-
 // rows idx(0..31) of Mat (ld = Mp) <- Q^T * rows, over all Mp columns.
 // Tiles of 32 x TW; the global loads of the next tile are issued into
 // registers before the current tile is computed.
@@ -384,15 +258,6 @@ __device__ void panel_rows(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
         const int cw = min(TW, Mp - c0);          // multiple of 32
         const bool more = c0 + TW < Mp;
         if (more) load(c0 + TW);
-        if constexpr (sizeof(T) == 4) {
-            tile_rows_tc(Mat, Mp, bi, bj, c0, cw, Q, stage);
-            __syncthreads();
-            if (more) {
-                stash();
-                __syncthreads();
-            }
-            continue;
-        }
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -461,15 +326,6 @@ __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
         const int rh = min(TR, Mp - r0);
         const bool more = r0 + TR < Mp;
         if (more) load(r0 + TR);
-        if constexpr (sizeof(T) == 4) {
-            tile_cols_tc(Mat, Mp, bi, bj, r0, rh, Q, stage);
-            __syncthreads();
-            if (more) {
-                stash();
-                __syncthreads();
-            }
-            continue;
-        }
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -497,77 +353,6 @@ __device__ void panel_cols(T* Mat, int Mp, int bi, int bj, const T* Q, T* stage)
             stash();
             __syncthreads();
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 panel tiles of one step as a pipeline: the tiles of all of this CTA's
-// pairs (phase A: the row tiles of G and of Vt; phase B: the column tiles of
-// G) are streamed through two shared buffers with cp.async, so the loads of
-// tile j+1 are in flight while tile j is multiplied on the tensor cores.
-// Tiles of one phase touch disjoint parts of G and Vt.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-struct PanelJob {
-    float* mat;   // G or Vt
-    int bi, bj;   // block pair
-    int q;        // index of the pair's Q
-    int at;       // first column (row tile) or first row (column tile)
-};
-
-__device__ __forceinline__ void issue_row_tile(const PanelJob& j, int Mp, float* buf) {
-    constexpr int TW = JSmem<float>::TW, SLD = JSmem<float>::RSLD;
-    const int cw = min(TW, Mp - j.at);
-    for (int it = threadIdx.x; it < kB2 * (TW / 4); it += kJT) {
-        const int k = it / (TW / 4), c = (it % (TW / 4)) * 4;
-        if (c < cw) cp_async16(buf + k * SLD + c, j.mat + (int64_t)gidx(j.bi, j.bj, k) * Mp + j.at + c);
-    }
-}
-
-__device__ __forceinline__ void issue_col_tile(const PanelJob& j, int Mp, float* buf) {
-    constexpr int TR = JSmem<float>::TR, SLD = JSmem<float>::CSLD;
-    const int rh = min(TR, Mp - j.at);
-    for (int it = threadIdx.x; it < TR * (kB2 / 4); it += kJT) {
-        const int r = it / (kB2 / 4), k = (it % (kB2 / 4)) * 4;
-        if (r < rh) cp_async16(buf + r * SLD + k, j.mat + (int64_t)(j.at + r) * Mp + gidx(j.bi, j.bj, k));
-    }
-}
-
-// rows (cols = false) or columns (cols = true) phase over njobs tiles.
-template <bool kCols>
-__device__ void run_panel_jobs(const PanelJob* jobs, int njobs, int Mp, const float* Qs,
-                               float* stage) {
-    constexpr int LD = JSmem<float>::LD, STAGE = JSmem<float>::STAGE;
-    if (njobs == 0) return;
-    auto issue = [&](int j) {
-        float* buf = stage + (j & 1) * STAGE;
-        if constexpr (kCols) issue_col_tile(jobs[j], Mp, buf);
-        else issue_row_tile(jobs[j], Mp, buf);
-        cp_async_commit();
-    };
-    issue(0);
-    for (int j = 0; j < njobs; ++j) {
-        if (j + 1 < njobs) {
-            issue(j + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const PanelJob& jb = jobs[j];
-        const float* Q = Qs + (size_t)jb.q * kB2 * LD;
-        const float* buf = stage + (j & 1) * STAGE;
-        if constexpr (kCols)
-            tile_cols_tc(jb.mat, Mp, jb.bi, jb.bj, jb.at, min(JSmem<float>::TR, Mp - jb.at), Q, buf);
-        else
-            tile_rows_tc(jb.mat, Mp, jb.bi, jb.bj, jb.at, min(JSmem<float>::TW, Mp - jb.at), Q, buf);
-        __syncthreads();
     }
 }
 
@@ -600,7 +385,6 @@ __device__ void jacobi_matrix(T* __restrict__ G, T* __restrict__ Vt, int Mp, int
     __shared__ int rot_flag;
     __shared__ int decision;
     __shared__ T floor_sh;
-    __shared__ __align__(16) unsigned char jobs_sh[16 * 2 * 4 * sizeof(PanelJob)];
 
     for (int64_t e = (int64_t)crank * kJT + threadIdx.x; e < (int64_t)Mp * Mp;
          e += (int64_t)csize * kJT) {
@@ -643,58 +427,21 @@ __device__ void jacobi_matrix(T* __restrict__ G, T* __restrict__ Vt, int Mp, int
                               rqs + warp * kB, tol, floor_abs, rotated);
             }
             __syncthreads();
-            if constexpr (sizeof(T) == 4) {
-                // job lists (identical in every thread; built in registers on the fly)
-                const int ntile = (Mp + JSmem<float>::TW - 1) / JSmem<float>::TW;
-                PanelJob* jobs = reinterpret_cast<PanelJob*>(jobs_sh);
-                int nj = 0;
-                if (threadIdx.x == 0) {
-                    for (int t = 0; t < nmine; ++t) {
-                        int bi, bj;
-                        circle_pair(nb, step, crank + t * csize, bi, bj);
-                        for (int m = 0; m < 2; ++m)
-                            for (int c = 0; c < ntile; ++c)
-                                jobs[nj++] = PanelJob{reinterpret_cast<float*>(m ? Vt : G), bi, bj, t,
-                                                      c * JSmem<float>::TW};
-                    }
-                }
-                __syncthreads();
-                nj = nmine * 2 * ntile;
-                run_panel_jobs<false>(jobs, nj, Mp, reinterpret_cast<const float*>(Qs),
-                                      reinterpret_cast<float*>(stage));
-                owner_sync<kCluster>();
-                const int ntr = (Mp + JSmem<float>::TR - 1) / JSmem<float>::TR;
-                if (threadIdx.x == 0) {
-                    int n2 = 0;
-                    for (int t = 0; t < nmine; ++t) {
-                        int bi, bj;
-                        circle_pair(nb, step, crank + t * csize, bi, bj);
-                        for (int r = 0; r < ntr; ++r)
-                            jobs[n2++] = PanelJob{reinterpret_cast<float*>(G), bi, bj, t,
-                                                  r * JSmem<float>::TR};
-                    }
-                }
-                __syncthreads();
-                run_panel_jobs<true>(jobs, nmine * ntr, Mp, reinterpret_cast<const float*>(Qs),
-                                     reinterpret_cast<float*>(stage));
-                owner_sync<kCluster>();
-            } else {
-                for (int t = 0; t < nmine; ++t) {
-                    int bi, bj;
-                    circle_pair(nb, step, crank + t * csize, bi, bj);
-                    const T* Q = Qs + (size_t)t * kB2 * LD;
-                    panel_rows<T>(G, Mp, bi, bj, Q, stage);
-                    panel_rows<T>(Vt, Mp, bi, bj, Q, stage);
-                }
-                owner_sync<kCluster>();
-                // phase B: columns of G
-                for (int t = 0; t < nmine; ++t) {
-                    int bi, bj;
-                    circle_pair(nb, step, crank + t * csize, bi, bj);
-                    panel_cols<T>(G, Mp, bi, bj, Qs + (size_t)t * kB2 * LD, stage);
-                }
-                owner_sync<kCluster>();
+            for (int t = 0; t < nmine; ++t) {
+                int bi, bj;
+                circle_pair(nb, step, crank + t * csize, bi, bj);
+                const T* Q = Qs + (size_t)t * kB2 * LD;
+                panel_rows<T>(G, Mp, bi, bj, Q, stage);
+                panel_rows<T>(Vt, Mp, bi, bj, Q, stage);
             }
+            owner_sync<kCluster>();
+            // phase B: columns of G
+            for (int t = 0; t < nmine; ++t) {
+                int bi, bj;
+                circle_pair(nb, step, crank + t * csize, bi, bj);
+                panel_cols<T>(G, Mp, bi, bj, Qs + (size_t)t * kB2 * LD, stage);
+            }
+            owner_sync<kCluster>();
         }
         ++sweep;
         // OR of the rotation flags over the owners
@@ -822,7 +569,6 @@ __device__ __forceinline__ void mma_split(float (&d)[4], const uint32_t (&ah)[4]
     mma_f16(d, ah, bh0, bh1);
 }
 
-__device__ __forceinline__ uint32_t ldcg_u32(const uint32_t* p) { return __ldcg(p); }
 // rotation words from the CTA's shared copy (kS) or from L2
 template <bool kS>
 __device__ __forceinline__ uint32_t ldq(const uint32_t* p) {
@@ -1320,7 +1066,6 @@ k_jacobi4(float* __restrict__ Gall, float* __restrict__ Vall, int Mp, int csize,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int crank = (int)cg::this_cluster().block_rank();
     const int mat = blockIdx.x / csize;
-    const int np = Mp / kB2;
     jacobi4_matrix<true>(Gall + (int64_t)mat * Mp * Mp, Vall + (int64_t)mat * Mp * Mp, Mp, csize,
                          crank, max_sweeps, tol, sweeps_out + mat,
                          qall + (size_t)mat * jwork_words(Mp), smem_raw);

@@ -100,13 +100,14 @@ struct Request {
     int slot = -1;
     cudaEvent_t done_ev = nullptr;
     bool inject_alloc = false, inject_bad_csc = false;
+    void* direct_v = nullptr;   // device address of a page-locked h_V (written in place)
 };
 
 struct Layout {
     size_t plan, col_ptr, row_idx, vals, sigma, U, V, rank, total;
 };
 
-Layout layout(const svd_desc& d, size_t plan_bytes) {
+Layout layout(const svd_desc& d, size_t plan_bytes, bool v_buffer) {
     const int64_t k = d.k > 0 ? d.k : std::min<int64_t>(d.M, d.N);
     const size_t sv = d.value_type == SVD_VALUE_F32 ? 4 : 8;
     const size_t sV = d.precision == SVD_PREC_MIXED ? 4 : 8;
@@ -119,7 +120,7 @@ Layout layout(const svd_desc& d, size_t plan_bytes) {
     L.vals = take(sv * (size_t)d.nnz);
     L.sigma = take(sizeof(double) * (size_t)k);
     L.U = take(sizeof(double) * (size_t)d.M * (size_t)k);
-    L.V = take((d.flags & SVD_FLAG_SKIP_V) ? 1 : sV * (size_t)d.N * (size_t)k);
+    L.V = take((d.flags & SVD_FLAG_SKIP_V) || !v_buffer ? 1 : sV * (size_t)d.N * (size_t)k);
     L.rank = take(sizeof(int32_t));
     L.total = off;
     return L;
@@ -162,7 +163,7 @@ void finish(svd_server_s* s, Request* r, svd_status st) {
 svd_status start(svd_server_s* s, Request* r) {
     cudaStream_t st = s->streams[r->slot];
     char* at = s->base + r->off;
-    const Layout L = layout(r->desc, r->plan_bytes);
+    const Layout L = layout(r->desc, r->plan_bytes, r->direct_v == nullptr);
     svd_status res = svd_plan_ws(&r->desc, at + L.plan, r->plan_bytes, &r->plan);
     if (res != SVD_OK) return res;
     const svd_desc& d = r->desc;
@@ -175,7 +176,7 @@ svd_status start(svd_server_s* s, Request* r) {
     void* va = at + L.vals;
     auto* sg = reinterpret_cast<double*>(at + L.sigma);
     auto* U = reinterpret_cast<double*>(at + L.U);
-    void* V = at + L.V;
+    void* V = r->direct_v ? r->direct_v : at + L.V;
     auto* rk = reinterpret_cast<int32_t*>(at + L.rank);
     bool ok = cudaMemcpyAsync(cp, r->io.h_col_ptr, sizeof(int64_t) * (d.N + 1),
                               cudaMemcpyHostToDevice, st) == cudaSuccess;
@@ -203,7 +204,7 @@ svd_status start(svd_server_s* s, Request* r) {
          cudaSuccess;
     ok = ok && cudaMemcpyAsync(r->io.h_U, U, sizeof(double) * d.M * k, cudaMemcpyDeviceToHost,
                                st) == cudaSuccess;
-    if (want_v)
+    if (want_v && !r->direct_v)
         ok = ok && cudaMemcpyAsync(r->io.h_V, V, sV * (size_t)d.N * k, cudaMemcpyDeviceToHost,
                                    st) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(r->io.h_rank, rk, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ==
@@ -336,7 +337,17 @@ svd_status svd_server_submit(svd_server_t s, const svd_request* req, uint64_t* t
     }
     r->io = *req;
     r->plan_bytes = plan_bytes;
-    r->total_bytes = layout(r->desc, plan_bytes).total;
+    // a page-locked V buffer is written in place by the device (no staging
+    // buffer in the pool, no copy); not with RandomChecker insertions, whose V
+    // correction uses atomic adds
+    if (req->h_V && !(r->desc.flags & SVD_FLAG_SKIP_V) && r->desc.rank_fix != SVD_RANKFIX_RANDOM) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, req->h_V) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer)
+            r->direct_v = at.devicePointer;
+        cudaGetLastError();
+    }
+    r->total_bytes = layout(r->desc, plan_bytes, r->direct_v == nullptr).total;
     std::lock_guard<std::mutex> lk(s->mu);
     if (r->total_bytes > s->budget) {
         ++s->n_rejected;

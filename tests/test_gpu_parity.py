@@ -235,6 +235,27 @@ def test_run_host_matches_run():
     assert hr[0] == out["rank"].item()
 
 
+def test_run_host_writes_pinned_v_directly():
+    """A page-locked V buffer is written by the device in place (no staging
+    copy); the result equals the device-buffer run."""
+    case = synth.small_uniform().with_values(np.float32)
+    dev = torch.device("cuda")
+    plan = rk.Plan(case.M, case.N, case.nnz, case.num_blocks, value_type="f32", precision="mixed")
+    out = rk.alloc_outputs(plan, with_patches=False)
+    plan.run(torch.from_numpy(case.col_ptr).to(dev), torch.from_numpy(case.row_idx).to(dev),
+             torch.from_numpy(case.vals).to(dev), out["sigma"], out["U"], out["V"], out["rank"])
+    plan.sync()
+    hs = torch.zeros(plan.k, dtype=torch.float64).pin_memory()
+    hU = torch.zeros(plan.k, plan.M, dtype=torch.float64).pin_memory()
+    hV = torch.full((plan.N, plan.k), float("nan"), dtype=torch.float32).pin_memory()
+    hr = torch.zeros(1, dtype=torch.int32).pin_memory()
+    plan.run_host(case.col_ptr, case.row_idx, case.vals, hs, hU, hV, hr)
+    assert torch.isfinite(hV).all()                 # every entry was written
+    np.testing.assert_allclose(hs.numpy(), out["sigma"].cpu().numpy(), rtol=1e-9)
+    np.testing.assert_allclose(np.abs(hV.numpy()), np.abs(out["V"].cpu().numpy()), rtol=0, atol=1e-5)
+    assert hr[0].item() == out["rank"].item()
+
+
 def test_check_csc_rejects_malformed():
     lib = rk.load_library()
     dev = torch.device("cuda")
