@@ -122,9 +122,10 @@ class ClockSampler:
 
 
 # DRAM traffic of one block-Jacobi launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), per matrix, with the hash of the kernel source it was taken on;
-# reported as null once the source changes.  See profiles/k_jacobi_f32_zipf_wide_250k.md.
-JACOBI_TRAFFIC = {"source_sha256_16": "b5bdde1ed4528738", "bytes_per_matrix": 19.917312e6 / 16}
+# dram__bytes_write.sum) on a 16-matrix launch (zipf_wide with 250k columns), per matrix,
+# with the hash of the kernel source it was taken on; reported as null once the source
+# changes.  See profiles/k_jacobi4_zipf_wide_250k.md.
+JACOBI_TRAFFIC = {"source_sha256_16": "d2d23d852db35f79", "bytes_per_matrix": (17236736 + 2764032) / 16}
 
 
 def source_hash(rel: str) -> str:
