@@ -267,16 +267,16 @@ k_oz_gemm(int m, int n, int64_t kpad, int64_t kc, const uint16_t* __restrict__ A
         __syncthreads();
         const uint32_t sa = sbase + buf * OzSmem<S>::STAGE;
         const uint32_t sb = sa + S * OzSmem<S>::A_BYTES;
-#pragma unroll
-        for (int t = 2; t <= S + 1; ++t) {
-            float f[2][4][4];
+        // weight classes t = a + b in turn; class t's products go to one of two
+        // FP32 accumulator sets while the previous class's sums are folded,
+        // so the fold never waits for the tensor pipe to drain
+        auto class_mma = [&](int t, float (&f)[2][4][4]) {
 #pragma unroll
             for (int x = 0; x < 2; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y)
 #pragma unroll
                     for (int z = 0; z < 4; ++z) f[x][y][z] = 0.f;
-#pragma unroll
 #pragma unroll 1
             for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
@@ -305,16 +305,27 @@ k_oz_gemm(int m, int n, int64_t kpad, int64_t kc, const uint16_t* __restrict__ A
                                    bfr[nj >> 1][(nj & 1) * 2 + 1]);
                 }
             }
-            // fold the exact stage sums of this weight class
-            const int sh = 8 * (S + 1 - t);
+        };
+        // fold the exact stage sums of class t (weight 2^(8 (S + 1 - t)))
+        auto fold = [&](int t, const float (&f)[2][4][4]) {
+            const long long w = 1ll << (8 * (S + 1 - t));
 #pragma unroll
             for (int x = 0; x < 2; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y)
 #pragma unroll
                     for (int z = 0; z < 4; ++z)
-                        acc[x][y][z] += (long long)__float2int_rn(f[x][y][z]) * (1ll << sh);
+                        acc[x][y][z] += (long long)__float2int_rn(f[x][y][z]) * w;
+        };
+        float fA[2][4][4], fB[2][4][4];
+        class_mma(2, fA);
+#pragma unroll
+        for (int t = 3; t <= S + 1; ++t) {
+            if (t & 1) { class_mma(t, fB); fold(t - 1, fA); }
+            else { class_mma(t, fA); fold(t - 1, fB); }
         }
+        if ((S + 1) & 1) fold(S + 1, fB);
+        else fold(S + 1, fA);
         __syncthreads();
     }
 
