@@ -357,20 +357,28 @@ def run_serve(args):
                 tickets.append(srv.submit(c.M, c.N, c.col_ptr, c.row_idx, c.vals, c.num_blocks, o,
                                           precision=prec))
             # requests still queued a grace period after the last arrival are
-            # cancelled and counted as dropped (an overloaded server would
-            # otherwise drain its backlog for minutes); admitted ones finish
+            # cancelled, all at once, and counted as dropped (an overloaded
+            # server would otherwise drain its backlog for minutes); admitted
+            # ones finish
             deadline = t_start + args.duration + args.grace
-            lat, fails, dropped, last_done = [], 0, 0, 0.0
-            first = None
+            status = {}
             for t in tickets:
                 call, st = srv.wait_status(t, max(0.0, deadline - time.perf_counter()))
-                if call == 7:      # SVD_ERR_TIMEOUT: not finished by the deadline
-                    if srv.cancel(t) == 0:
-                        srv.wait_status(t, 60.0)
-                        dropped += 1
-                        srv.release(t)
-                        continue
-                    st = srv.wait(t, timeout=600.0)
+                if call == 0:
+                    status[t] = st
+            dropped = 0
+            for t in tickets:
+                if t not in status and srv.cancel(t) == 0:
+                    srv.wait_status(t, 60.0)
+                    status[t] = None
+                    dropped += 1
+            lat, fails, last_done = [], 0, 0.0
+            first = None
+            for t in tickets:
+                if t in status and status[t] is None:
+                    srv.release(t)
+                    continue
+                st = status[t] if t in status else srv.wait(t, timeout=120.0)
                 ts, ta, td = srv.times(t)
                 first = ts if first is None else min(first, ts)
                 last_done = max(last_done, td)

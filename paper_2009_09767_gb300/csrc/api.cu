@@ -17,6 +17,7 @@
 #include "../../include/ranky.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "batch_engine.h"
 
 using namespace rk;
 
@@ -879,6 +880,8 @@ struct svd_batch_s {
     cudaEvent_t in_ev = nullptr, out_ev = nullptr;
     std::vector<RunIO> ios_seen;
     int64_t launches = 0;
+    size_t item_capacity = 0;            // JacobiItems the device list holds
+    JacobiItem* h_stage = nullptr;       // page-locked staging for asynchronous list uploads
 };
 
 namespace {
@@ -941,36 +944,48 @@ svd_status batch_enqueue(svd_batch_s* b, const RunIO* ios, cudaStream_t s) {
     return st;
 }
 
-bool same_ios(const std::vector<RunIO>& a, const RunIO* b, size_t n) {
-    if (a.size() != n) return false;
-    return memcmp(a.data(), b, sizeof(RunIO) * n) == 0;
-}
-
 }  // namespace
 
-extern "C" {
-
-svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, svd_batch_t* out) {
-    if (!out || n < 1 || !plans) return SVD_ERR_INVALID_ARG;
+svd_status batch_engine_create(int nstreams, size_t item_capacity, svd_batch_t* out) {
+    if (!out || nstreams < 1) return SVD_ERR_INVALID_ARG;
     *out = nullptr;
-    for (int i = 0; i < n; ++i)
-        if (!plans[i]) return SVD_ERR_INVALID_ARG;
     svd_batch_s* b = new (std::nothrow) svd_batch_s();
     if (!b) return SVD_ERR_OOM;
-    b->plans.assign(plans, plans + n);
-    b->use_graph = (flags & SVD_BATCH_GRAPH) != 0;
-    const int ns = std::min(n, 8);
+    item_capacity = std::max<size_t>(item_capacity, 1);
     bool ok = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->in_ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->out_ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
-    b->streams.resize(ns);
-    b->join_ev.resize(ns);
-    for (int i = 0; i < ns && ok; ++i) {
+    b->streams.resize(nstreams);
+    b->join_ev.resize(nstreams);
+    for (int i = 0; i < nstreams && ok; ++i) {
         ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
     }
-    // work lists
+    ok = ok && cudaMalloc(&b->d_items, sizeof(JacobiItem) * item_capacity) == cudaSuccess &&
+         cudaMalloc(&b->d_next, sizeof(int) * 4) == cudaSuccess &&
+         cudaHostAlloc(&b->h_stage, sizeof(JacobiItem) * item_capacity, cudaHostAllocDefault) == cudaSuccess;
+    b->item_capacity = item_capacity;
+    if (!ok) {
+        cudaGetLastError();
+        svd_batch_free(b);
+        return SVD_ERR_OOM;
+    }
+    *out = b;
+    return SVD_OK;
+}
+
+svd_status batch_engine_assign(svd_batch_t b, int n, const svd_plan_t* plans, cudaStream_t stream) {
+    if (!b || n < 1 || !plans) return SVD_ERR_INVALID_ARG;
+    // (the previous plans were detached, or belong to a batch being built:
+    // they are not touched here, they may be gone)
+    b->plans.assign(plans, plans + n);
+    b->outsized.clear();
+    for (int w = 0; w < 4; ++w) { b->maxmp[w] = 0; b->tol[w] = 0.0; }
+    b->sweeps_cap = 40;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    b->captured = false;
+    // work lists: [blocks f32 | blocks f64 | merges f32 | merges f64]
     std::vector<JacobiItem> lists[4];
     const int cap32 = jacobi_item_max_mp(false), cap64 = jacobi_item_max_mp(true);
     for (int i = 0; i < n; ++i) {
@@ -1010,18 +1025,55 @@ svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, s
         b->count[w] = (int)lists[w].size();
         total += lists[w].size();
     }
-    if (ok && total) {
-        ok = cudaMalloc(&b->d_items, sizeof(JacobiItem) * total) == cudaSuccess &&
-             cudaMalloc(&b->d_next, sizeof(int) * 4) == cudaSuccess;
-        for (int w = 0; w < 4 && ok; ++w)
-            if (b->count[w])
-                ok = cudaMemcpy(b->d_items + b->offset[w], lists[w].data(),
-                                sizeof(JacobiItem) * b->count[w], cudaMemcpyHostToDevice) == cudaSuccess;
-    }
-    if (!ok) {
-        cudaGetLastError();
+    if (total > b->item_capacity) return SVD_ERR_INVALID_ARG;
+    if (!total) return SVD_OK;
+    for (int w = 0; w < 4; ++w)
+        std::copy(lists[w].begin(), lists[w].end(), b->h_stage + b->offset[w]);
+    // asynchronous on the caller's stream (from page-locked staging, which is
+    // not touched again before the pass that reads the lists has run), or
+    // synchronous when no stream is given
+    const cudaError_t e = stream ? cudaMemcpyAsync(b->d_items, b->h_stage, sizeof(JacobiItem) * total,
+                                                   cudaMemcpyHostToDevice, stream)
+                                 : cudaMemcpy(b->d_items, b->h_stage, sizeof(JacobiItem) * total,
+                                              cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaGetLastError(); return SVD_ERR_CUDA; }
+    return SVD_OK;
+}
+
+void batch_engine_detach(svd_batch_t b) {
+    if (!b) return;
+    for (svd_plan_s* p : b->plans)   // plans that leave the batch keep no stream of it
+        for (cudaStream_t w : b->streams)
+            if (p->last_stream == w || p->last_stream == b->cap_stream) p->last_stream = nullptr;
+    b->plans.clear();
+}
+
+namespace {
+
+bool same_ios(const std::vector<RunIO>& a, const RunIO* b, size_t n) {
+    if (a.size() != n) return false;
+    return memcmp(a.data(), b, sizeof(RunIO) * n) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, svd_batch_t* out) {
+    if (!out || n < 1 || !plans) return SVD_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!plans[i]) return SVD_ERR_INVALID_ARG;
+    size_t items = 0;
+    for (int i = 0; i < n; ++i) items += (size_t)plans[i]->D + 1;
+    svd_batch_t b = nullptr;
+    svd_status st = batch_engine_create(std::min(n, 8), items, &b);
+    if (st != SVD_OK) return st;
+    b->use_graph = (flags & SVD_BATCH_GRAPH) != 0;
+    st = batch_engine_assign(b, n, plans, nullptr);
+    if (st != SVD_OK) {
         svd_batch_free(b);
-        return SVD_ERR_OOM;
+        return st;
     }
     *out = b;
     return SVD_OK;
@@ -1121,6 +1173,7 @@ void svd_batch_free(svd_batch_t b) {
     if (b->out_ev) cudaEventDestroy(b->out_ev);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_next) cudaFree(b->d_next);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
     delete b;
 }
 

@@ -5,11 +5,16 @@
 // order whenever a stream slot is free and the request fits in what is left
 // of the device-memory budget, places its plan workspace, CSC and outputs in
 // one allocation from a first-fit pool over a single budget-sized device
-// buffer, and enqueues host->device copies, svd_run and device->host copies
-// on the slot's stream.  Requests that arrive while others are running are
+// buffer, and enqueues host->device copies, the SVD and device->host copies
+// on the slot's stream.  Consecutive small requests waiting together are
+// admitted into one slot as a group and run as ONE batched pass (the slot's
+// reusable batch: all their block eigensolves in one persistent launch, all
+// their merge eigensolves in another); a large request, or one arriving
+// alone, runs by itself.  Requests that arrive while others are running are
 // admitted as slots and memory free up, so their kernels overlap on the GPU.
-// Completion is detected by polling a CUDA event per request; the request's
-// pool memory and plan are released at once and its latency stamped.
+// Completion is detected by polling one CUDA event per admitted group; the
+// requests' pool memory and plans are released at once and their latency
+// stamped.
 //
 // Fault injection for the tests is host-side only: a chosen ticket can be
 // made to fail its pool allocation (SVD_INJECT_ALLOC) or to have its CSC
@@ -31,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/ranky.h"
+#include "batch_engine.h"
 
 namespace {
 
@@ -87,6 +93,13 @@ private:
 
 enum State { kPending = 0, kRunning = 1, kDone = 2 };
 
+// Grouping: requests of at most kSmallM rows and kSmallBlocks blocks batch
+// together, up to kMaxGroup per pass and kEngineItems eigensolves.
+constexpr int kSmallM = 256;
+constexpr int kSmallBlocks = 16;
+constexpr int kMaxGroup = 64;
+constexpr size_t kEngineItems = kMaxGroup * (kSmallBlocks + 1);
+
 struct Request {
     uint64_t ticket = 0;
     svd_desc desc{};
@@ -101,6 +114,7 @@ struct Request {
     cudaEvent_t done_ev = nullptr;
     bool inject_alloc = false, inject_bad_csc = false;
     void* direct_v = nullptr;   // device address of a page-locked h_V (written in place)
+    char* base_at = nullptr;    // the request's pool allocation
 };
 
 struct Layout {
@@ -139,7 +153,8 @@ struct svd_server_s {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> pending;
-    std::vector<Request*> running;
+    std::vector<std::vector<Request*>> running;   // admitted groups (event of the first)
+    std::vector<svd_batch_t> engines;             // one reusable batch per slot
     std::unordered_map<uint64_t, Request*> all;
     std::thread worker;
     bool stop = false;
@@ -157,33 +172,42 @@ void finish(svd_server_s* s, Request* r, svd_status st) {
     if (st == SVD_OK) ++s->n_completed; else ++s->n_failed;
 }
 
-// Start one admitted request on its slot (scheduler thread, lock NOT held:
-// the copies from pageable host memory can block this thread).  Returns the
-// status; SVD_OK means the work is enqueued and r->done_ev recorded.
-svd_status start(svd_server_s* s, Request* r) {
-    cudaStream_t st = s->streams[r->slot];
-    char* at = s->base + r->off;
+// Device addresses of one placed request.
+struct Placed {
+    int64_t* cp;
+    int32_t* ri;
+    void* va;
+    double* sg;
+    double* U;
+    void* V;
+    int32_t* rk;
+    bool want_v;
+};
+
+// Place one admitted request's plan and copy its inputs on stream st
+// (scheduler thread, lock NOT held: copies from pageable host memory can
+// block this thread).
+svd_status setup(Request* r, cudaStream_t st, Placed& P) {
+    char* at = r->base_at;
     const Layout L = layout(r->desc, r->plan_bytes, r->direct_v == nullptr);
     svd_status res = svd_plan_ws(&r->desc, at + L.plan, r->plan_bytes, &r->plan);
     if (res != SVD_OK) return res;
     const svd_desc& d = r->desc;
-    const int64_t k = d.k > 0 ? d.k : std::min<int64_t>(d.M, d.N);
     const size_t sv = d.value_type == SVD_VALUE_F32 ? 4 : 8;
-    const size_t sV = d.precision == SVD_PREC_MIXED ? 4 : 8;
-    const bool want_v = r->io.h_V && !(d.flags & SVD_FLAG_SKIP_V);
-    auto* cp = reinterpret_cast<int64_t*>(at + L.col_ptr);
-    auto* ri = reinterpret_cast<int32_t*>(at + L.row_idx);
-    void* va = at + L.vals;
-    auto* sg = reinterpret_cast<double*>(at + L.sigma);
-    auto* U = reinterpret_cast<double*>(at + L.U);
-    void* V = r->direct_v ? r->direct_v : at + L.V;
-    auto* rk = reinterpret_cast<int32_t*>(at + L.rank);
-    bool ok = cudaMemcpyAsync(cp, r->io.h_col_ptr, sizeof(int64_t) * (d.N + 1),
+    P.want_v = r->io.h_V && !(d.flags & SVD_FLAG_SKIP_V);
+    P.cp = reinterpret_cast<int64_t*>(at + L.col_ptr);
+    P.ri = reinterpret_cast<int32_t*>(at + L.row_idx);
+    P.va = at + L.vals;
+    P.sg = reinterpret_cast<double*>(at + L.sigma);
+    P.U = reinterpret_cast<double*>(at + L.U);
+    P.V = r->direct_v ? r->direct_v : at + L.V;
+    P.rk = reinterpret_cast<int32_t*>(at + L.rank);
+    bool ok = cudaMemcpyAsync(P.cp, r->io.h_col_ptr, sizeof(int64_t) * (d.N + 1),
                               cudaMemcpyHostToDevice, st) == cudaSuccess;
     if (d.nnz > 0) {
-        ok = ok && cudaMemcpyAsync(ri, r->io.h_row_idx, sizeof(int32_t) * d.nnz,
+        ok = ok && cudaMemcpyAsync(P.ri, r->io.h_row_idx, sizeof(int32_t) * d.nnz,
                                    cudaMemcpyHostToDevice, st) == cudaSuccess;
-        ok = ok && cudaMemcpyAsync(va, r->io.h_vals, sv * d.nnz, cudaMemcpyHostToDevice, st) ==
+        ok = ok && cudaMemcpyAsync(P.va, r->io.h_vals, sv * d.nnz, cudaMemcpyHostToDevice, st) ==
                        cudaSuccess;
     }
     if (!ok) { cudaGetLastError(); return SVD_ERR_CUDA; }
@@ -191,33 +215,89 @@ svd_status start(svd_server_s* s, Request* r) {
         // the host-side stand-in for a malformed request: a column pointer
         // that does not end at nnz, which the CSC check rejects
         int64_t bad = d.nnz + 1;
-        cudaMemcpyAsync(cp + d.N, &bad, sizeof(bad), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(P.cp + d.N, &bad, sizeof(bad), cudaMemcpyHostToDevice, st);
         cudaStreamSynchronize(st);
     }
     if (d.flags & SVD_FLAG_CHECK_CSC) {
-        res = svd_check_csc(d.M, d.N, d.nnz, cp, ri, st);
+        res = svd_check_csc(d.M, d.N, d.nnz, P.cp, P.ri, st);
         if (res != SVD_OK) return res;
     }
-    res = svd_run(r->plan, cp, ri, va, sg, U, want_v ? V : nullptr, rk, nullptr, nullptr, st);
-    if (res != SVD_OK) return res;
-    ok = cudaMemcpyAsync(r->io.h_sigma, sg, sizeof(double) * k, cudaMemcpyDeviceToHost, st) ==
-         cudaSuccess;
-    ok = ok && cudaMemcpyAsync(r->io.h_U, U, sizeof(double) * d.M * k, cudaMemcpyDeviceToHost,
+    return SVD_OK;
+}
+
+// Results back to the request's host buffers on stream st.
+svd_status copy_back(Request* r, const Placed& P, cudaStream_t st) {
+    const svd_desc& d = r->desc;
+    const int64_t k = d.k > 0 ? d.k : std::min<int64_t>(d.M, d.N);
+    const size_t sV = d.precision == SVD_PREC_MIXED ? 4 : 8;
+    bool ok = cudaMemcpyAsync(r->io.h_sigma, P.sg, sizeof(double) * k, cudaMemcpyDeviceToHost, st) ==
+              cudaSuccess;
+    ok = ok && cudaMemcpyAsync(r->io.h_U, P.U, sizeof(double) * d.M * k, cudaMemcpyDeviceToHost,
                                st) == cudaSuccess;
-    if (want_v && !r->direct_v)
-        ok = ok && cudaMemcpyAsync(r->io.h_V, V, sV * (size_t)d.N * k, cudaMemcpyDeviceToHost,
+    if (P.want_v && !r->direct_v)
+        ok = ok && cudaMemcpyAsync(r->io.h_V, P.V, sV * (size_t)d.N * k, cudaMemcpyDeviceToHost,
                                    st) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(r->io.h_rank, rk, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ==
+    ok = ok && cudaMemcpyAsync(r->io.h_rank, P.rk, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ==
                    cudaSuccess;
-    ok = ok && cudaEventRecord(r->done_ev, st) == cudaSuccess;
     if (!ok) { cudaGetLastError(); return SVD_ERR_CUDA; }
     return SVD_OK;
+}
+
+// Start one admitted group on its slot (lock NOT held): place every request,
+// run the group (one request: svd_run; several: one batched pass on the
+// slot's batch) and queue the copies back; the group's event is recorded on
+// the slot stream after all of it.  res[i] is request i's status; the
+// requests with SVD_OK form the running group (event: the first one's).
+void start_group(svd_server_s* s, const std::vector<Request*>& g, std::vector<svd_status>& res) {
+    const int slot = g[0]->slot;
+    cudaStream_t st = s->streams[slot];
+    res.assign(g.size(), SVD_OK);
+    std::vector<Placed> P(g.size());
+    std::vector<size_t> live;
+    for (size_t i = 0; i < g.size(); ++i) {
+        res[i] = setup(g[i], st, P[i]);
+        if (res[i] == SVD_OK) live.push_back(i);
+    }
+    svd_status run = SVD_OK;
+    if (live.size() == 1) {
+        const size_t i = live[0];
+        run = svd_run(g[i]->plan, P[i].cp, P[i].ri, P[i].va, P[i].sg, P[i].U, P[i].want_v ? P[i].V : nullptr,
+                      P[i].rk, nullptr, nullptr, st);
+    } else if (live.size() > 1) {
+        std::vector<svd_plan_t> plans;
+        std::vector<svd_io> ios;
+        for (size_t i : live) {
+            plans.push_back(g[i]->plan);
+            ios.push_back(svd_io{P[i].cp, P[i].ri, P[i].va, P[i].sg, P[i].U,
+                                 P[i].want_v ? P[i].V : nullptr, P[i].rk, nullptr, nullptr});
+        }
+        run = batch_engine_assign(s->engines[slot], (int)plans.size(), plans.data(), st);
+        if (run == SVD_OK) run = svd_batch_run(s->engines[slot], ios.data(), st);
+    }
+    for (size_t i : live) {
+        res[i] = run;
+        if (res[i] == SVD_OK) res[i] = copy_back(g[i], P[i], st);
+    }
+    // the event of the first running request marks the whole group
+    for (size_t i : live)
+        if (res[i] == SVD_OK) {
+            if (cudaEventRecord(g[i]->done_ev, st) != cudaSuccess) {
+                cudaGetLastError();
+                for (size_t j : live) res[j] = SVD_ERR_CUDA;
+            }
+            break;
+        }
 }
 
 void release(svd_server_s* s, Request* r) {
     if (r->plan) { svd_free(r->plan); r->plan = nullptr; }
     if (r->total_bytes) { s->pool->release(r->off, r->total_bytes); r->total_bytes = 0; }
-    if (r->slot >= 0) { s->slot_busy[r->slot] = 0; r->slot = -1; }
+    r->slot = -1;
+}
+
+bool small_request(const Request* r) {
+    return r->desc.M <= kSmallM && r->desc.num_blocks <= kSmallBlocks && !r->inject_alloc &&
+           !r->inject_bad_csc;
 }
 
 void scheduler(svd_server_s* s) {
@@ -225,61 +305,95 @@ void scheduler(svd_server_s* s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         bool progressed = false;
-        // completions
+        // completions: one event per running group
         for (size_t i = 0; i < s->running.size();) {
-            Request* r = s->running[i];
-            const cudaError_t q = cudaEventQuery(r->done_ev);
+            std::vector<Request*>& g = s->running[i];
+            const cudaError_t q = cudaEventQuery(g[0]->done_ev);
             if (q == cudaErrorNotReady) { ++i; continue; }
-            svd_status st = q == cudaSuccess ? svd_sync(r->plan) : SVD_ERR_CUDA;
             if (q != cudaSuccess) cudaGetLastError();
-            release(s, r);
-            finish(s, r, st);
+            const int slot = g[0]->slot;
+            std::vector<svd_status> sts(g.size());
+            for (size_t j = 0; j < g.size(); ++j)
+                sts[j] = q == cudaSuccess ? svd_sync(g[j]->plan) : SVD_ERR_CUDA;
+            // a batched group's plans leave the slot's batch before they are freed
+            if (g.size() > 1) batch_engine_detach(s->engines[slot]);
+            for (size_t j = 0; j < g.size(); ++j) {
+                release(s, g[j]);
+                finish(s, g[j], sts[j]);
+            }
+            s->slot_busy[slot] = 0;
             s->running.erase(s->running.begin() + i);
             progressed = true;
         }
-        // admissions, in arrival order: reserve a slot and pool memory
-        std::vector<Request*> admitted;
+        // admissions, in arrival order: reserve a slot and pool memory; a small
+        // request takes the small ones queued right behind it into its group
+        std::vector<std::vector<Request*>> admitted;
         while (!s->pending.empty()) {
-            Request* r = s->pending.front();
             int slot = -1;
             for (int i = 0; i < s->max_inflight; ++i)
                 if (!s->slot_busy[i]) { slot = i; break; }
             if (slot < 0) break;
+            Request* r = s->pending.front();
             if (r->inject_alloc) {
                 s->pending.pop_front();
                 finish(s, r, SVD_ERR_OOM);
                 progressed = true;
                 continue;
             }
-            size_t off = 0;
-            if (!s->pool->alloc(r->total_bytes, &off)) break;   // wait for memory
-            s->pending.pop_front();
-            r->off = off;
-            r->slot = slot;
+            std::vector<Request*> g;
+            size_t items = 0;
+            while (!s->pending.empty()) {
+                Request* q = s->pending.front();
+                if (!g.empty() && (!small_request(g[0]) || !small_request(q) ||
+                                   (int)g.size() >= kMaxGroup ||
+                                   items + q->desc.num_blocks + 1 > kEngineItems))
+                    break;
+                size_t off = 0;
+                if (!s->pool->alloc(q->total_bytes, &off)) break;   // wait for memory
+                s->pending.pop_front();
+                q->off = off;
+                q->base_at = s->base + off;
+                q->slot = slot;
+                q->t_admit = now_s();
+                q->state = kRunning;
+                items += q->desc.num_blocks + 1;
+                g.push_back(q);
+            }
+            if (g.empty()) break;
             s->slot_busy[slot] = 1;
-            r->t_admit = now_s();
-            r->state = kRunning;
-            admitted.push_back(r);
+            admitted.push_back(std::move(g));
         }
         if (!admitted.empty()) {
             // enqueue their work without holding the lock
             lk.unlock();
-            std::vector<svd_status> res(admitted.size());
+            std::vector<std::vector<svd_status>> res(admitted.size());
             for (size_t i = 0; i < admitted.size(); ++i) {
-                res[i] = start(s, admitted[i]);
+                start_group(s, admitted[i], res[i]);
                 // a request that failed part-way may still have copies in flight
-                // on its stream: let them land before its memory is reused
-                if (res[i] != SVD_OK) cudaStreamSynchronize(s->streams[admitted[i]->slot]);
+                // on the slot's stream: let them land before its memory is reused
+                for (svd_status st : res[i])
+                    if (st != SVD_OK) { cudaStreamSynchronize(s->streams[admitted[i][0]->slot]); break; }
             }
             lk.lock();
             for (size_t i = 0; i < admitted.size(); ++i) {
-                Request* r = admitted[i];
-                if (res[i] == SVD_OK) {
-                    s->running.push_back(r);
-                } else {
-                    release(s, r);
-                    finish(s, r, res[i]);
+                std::vector<Request*> run;
+                const int slot = admitted[i][0]->slot;
+                for (size_t j = 0; j < admitted[i].size(); ++j)
+                    if (res[i][j] != SVD_OK) {   // a failed request's plan must leave the batch
+                        batch_engine_detach(s->engines[slot]);
+                        break;
+                    }
+                for (size_t j = 0; j < admitted[i].size(); ++j) {
+                    Request* r = admitted[i][j];
+                    if (res[i][j] == SVD_OK) {
+                        run.push_back(r);
+                    } else {
+                        release(s, r);
+                        finish(s, r, res[i][j]);
+                    }
                 }
+                if (run.empty()) s->slot_busy[slot] = 0;
+                else s->running.push_back(std::move(run));
             }
             progressed = true;
         }
@@ -316,6 +430,18 @@ svd_status svd_server_create(size_t budget_bytes, int32_t max_inflight, svd_serv
     s->streams.resize(max_inflight);
     s->slot_busy.assign(max_inflight, 0);
     for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    s->engines.assign(max_inflight, nullptr);
+    for (auto& e : s->engines) {
+        if (batch_engine_create(4, kEngineItems, &e) != SVD_OK) {
+            for (auto& f : s->engines)
+                if (f) svd_batch_free(f);
+            for (auto& st : s->streams) cudaStreamDestroy(st);
+            cudaFree(s->base);
+            delete s->pool;
+            delete s;
+            return SVD_ERR_OOM;
+        }
+    }
     s->worker = std::thread(scheduler, s);
     *out = s;
     return SVD_OK;
@@ -336,6 +462,7 @@ svd_status svd_server_submit(svd_server_t s, const svd_request* req, uint64_t* t
         r->desc.block_col_bounds = r->bounds.data();
     }
     r->io = *req;
+    if (!req->h_V) r->desc.flags |= SVD_FLAG_SKIP_V;   // no V wanted: none computed
     r->plan_bytes = plan_bytes;
     // a page-locked V buffer is written in place by the device (no staging
     // buffer in the pool, no copy); not with RandomChecker insertions, whose V
@@ -456,7 +583,9 @@ svd_status svd_server_stats(svd_server_t s, int64_t* out8) {
     out8[1] = s->n_completed;
     out8[2] = s->n_failed;
     out8[3] = s->n_rejected;
-    out8[4] = (int64_t)s->running.size();
+    int64_t nrun = 0;
+    for (const auto& g : s->running) nrun += (int64_t)g.size();
+    out8[4] = nrun;
     out8[5] = (int64_t)s->pending.size();
     out8[6] = (int64_t)s->pool->used();
     out8[7] = (int64_t)s->pool->peak();
@@ -481,6 +610,8 @@ void svd_server_destroy(svd_server_t s) {
         if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
         delete kv.second;
     }
+    for (auto& e : s->engines)
+        if (e) svd_batch_free(e);
     for (auto& st : s->streams) cudaStreamDestroy(st);
     cudaFree(s->base);
     delete s->pool;
