@@ -118,3 +118,35 @@ def test_cancel_timeout_and_injected_faults():
     for t in (t0, t1, t2, t3, t4, t5):
         srv.release(t)
     srv.close()
+
+
+def test_group_member_failure_is_isolated():
+    """Small requests queued together run as one batched group; a member whose
+    CSC is malformed (rejected by the requested structural check) fails alone
+    and its group-mates finish with correct results."""
+    cases = _requests(5, seed=21)
+    heavy = synth.random_dense_csc(np.random.default_rng(4), 512, 60000, 0.01, dtype=np.float32)
+    heavy.num_blocks = 8
+    srv = rk.Server(4 << 30, max_inflight=1)
+    t_heavy, _ = _submit(srv, heavy)               # holds the only slot: the rest queue up
+    tickets = []
+    for i, c in enumerate(cases):
+        cp = c.col_ptr.copy()
+        if i == 2:
+            cp[-1] += 1                            # col_ptr[N] != nnz: malformed
+        k = min(c.M, c.N)
+        o = rk.host_outputs(c.M, c.N, k, "mixed")
+        tickets.append((srv.submit(c.M, c.N, cp, c.row_idx, c.vals, c.num_blocks, o,
+                                   precision="mixed", flags=rk.FLAG_CHECK_CSC), o, c))
+    assert srv.wait(t_heavy) == 0
+    for i, (t, o, c) in enumerate(tickets):
+        st = srv.wait(t)
+        if i == 2:
+            assert st == 2                         # SVD_ERR_INVALID_CSC
+            continue
+        assert st == 0
+        s_ref, _, _, _ = oracle.svd_csc(c.col_ptr, c.row_idx, c.vals.astype(np.float64), c.M, c.N)
+        sigma_check(o["sigma"], s_ref[:len(o["sigma"])], 1e-4, 1e-6)
+    stats = srv.stats()
+    assert stats["failed"] == 1 and stats["pool_used"] == 0
+    srv.close()
