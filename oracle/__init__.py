@@ -24,6 +24,16 @@ What each function follows:
 * ``random_patches``: RandomChecker, Algorithm 2, with Philox4x32-10 keyed by
   (seed) and counted by (row, block).  Rows that are empty in all of A are not
   lonely nodes (they are excluded from the fix).
+* ``neighbor_list`` / ``neighbor_patches``: NeighborChecker, Algorithm 3,
+  with the two lists built literally as multisets in ``oracle.c``, and
+  neighbourRandomChecker, Algorithm 4, read as RandomChecker only where the
+  neighbour list is empty (Tables II and III print identical errors, which a
+  second insertion would not give).  The column is entry floor(x T / 2^64)
+  of the sorted list, x the 64-bit Philox word counted by (row, block, 1).
+* ``neighbor_patches_sparse``: the same choice evaluated in closed form from
+  the sparsity pattern B of A: column n of block d appears
+  (B B^T)[m, :] B[:, n] times in row m's neighbour list.  Used where a dense
+  copy does not fit; pinned against the literal lists.
 * ``gram_dense``: Eq. 2's block cross product by plain summation.
 * ``residuals``: a-posteriori residual bounds max(|A v - s u|, |A^T u - s v|)
   for triplets of matrices too large to densify; each bounds the distance
@@ -75,6 +85,16 @@ def _load():
                 ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                 ctypes.c_int64, ctypes.c_int64]
             lib.ro_random_patch_col.restype = ctypes.c_int64
+            lib.ro_neighbor_list.argtypes = [P, ctypes.c_int32, ctypes.c_int64, P,
+                                             ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, P, ctypes.c_int64]
+            lib.ro_neighbor_list.restype = ctypes.c_int64
+            lib.ro_neighbor_patch_col.argtypes = [P, ctypes.c_int32, ctypes.c_int64, P,
+                                                  ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_int32, ctypes.c_uint64, P]
+            lib.ro_neighbor_patch_col.restype = ctypes.c_int64
+            lib.ro_mulhi64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.ro_mulhi64.restype = ctypes.c_uint64
             lib.ro_lonely_dense.argtypes = [P, ctypes.c_int32, ctypes.c_int64, P,
                                             ctypes.c_int32, P, P]
             lib.ro_lonely_dense.restype = None
@@ -121,6 +141,112 @@ def random_patches(lonely: np.ndarray, bounds: np.ndarray, seed: int) -> np.ndar
             if lonely[d, m]:
                 out.append((m, random_patch_col(seed, d, m, lo, hi - lo)))
     return np.asarray(out, dtype=np.int64).reshape(-1, 2)
+
+
+# --------------------------------------------------------------------------
+# NeighborChecker (Algorithm 3) and neighbourRandomChecker (Algorithm 4)
+
+def neighbor_list(A: np.ndarray, bounds: np.ndarray, d: int, m: int) -> np.ndarray:
+    """Row m's neighbour list in block d (Algorithm 3, multiset), sorted."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M, N = A.shape
+    b = np.ascontiguousarray(bounds, dtype=np.int64)
+    D = b.shape[0] - 1
+    n = lib.ro_neighbor_list(_ptr(A), M, N, _ptr(b), D, d, m, None, 0)
+    if n < 0:
+        raise MemoryError("oracle: allocation failed")
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    lib.ro_neighbor_list(_ptr(A), M, N, _ptr(b), D, d, m, _ptr(out), n)
+    return out[:n]
+
+
+def neighbor_patch_col(A: np.ndarray, bounds: np.ndarray, d: int, m: int,
+                       seed: int) -> tuple[int, int]:
+    """(column, list length) NeighborChecker picks for lonely row m of block
+    d; column -1 when the list is empty."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M, N = A.shape
+    b = np.ascontiguousarray(bounds, dtype=np.int64)
+    D = b.shape[0] - 1
+    ln = np.zeros(1, dtype=np.int64)
+    col = lib.ro_neighbor_patch_col(_ptr(A), M, N, _ptr(b), D, d, m, seed, _ptr(ln))
+    if col == -2:
+        raise MemoryError("oracle: allocation failed")
+    return int(col), int(ln[0])
+
+
+def neighbor_patches(A: np.ndarray, bounds: np.ndarray, lonely: np.ndarray, seed: int,
+                     fallback_random: bool = False) -> np.ndarray:
+    """NeighborChecker (fallback_random=False) or neighbourRandomChecker for
+    every lonely (block d, row m) in (d, m) order.  Returns (P, 2) rows
+    (m, col); a lonely node with an empty neighbour list gets no insertion,
+    or the RandomChecker column with the fallback."""
+    D, M = lonely.shape
+    out = []
+    for d in range(D):
+        lo, hi = int(bounds[d]), int(bounds[d + 1])
+        for m in range(M):
+            if not lonely[d, m]:
+                continue
+            col, _ = neighbor_patch_col(A, bounds, d, m, seed)
+            if col < 0 and fallback_random:
+                col = random_patch_col(seed, d, m, lo, hi - lo)
+            if col >= 0:
+                out.append((m, col))
+    return np.asarray(out, dtype=np.int64).reshape(-1, 2)
+
+
+def mulhi64(a: int, b: int) -> int:
+    """High 64 bits of a*b as the C oracle forms them (draw -> list entry)."""
+    return int(_load().ro_mulhi64(a, b))
+
+
+def _philox_u64(seed: int, d: int, m: int) -> int:
+    w = philox4x32_10([m, d, 1, 0], [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])
+    return int(w[0]) | (int(w[1]) << 32)
+
+
+def neighbor_patches_sparse(col_ptr, row_idx, vals, M: int, bounds: np.ndarray,
+                            lonely: np.ndarray, seed: int,
+                            fallback_random: bool = False) -> np.ndarray:
+    """``neighbor_patches`` from the non-zero list: the multiplicity of column
+    n in row m's neighbour list of block d is (B B^T)[m, :] B[:, n], B the
+    0/1 pattern of A (exact integer products); the drawn entry is located by
+    a cumulative sum over the block's columns."""
+    import scipy.sparse as sp
+
+    col_ptr = np.asarray(col_ptr, dtype=np.int64)
+    N = col_ptr.shape[0] - 1
+    keep = np.asarray(vals) != 0
+    c_of = np.repeat(np.arange(N, dtype=np.int64), np.diff(col_ptr))
+    B = sp.csc_matrix((np.ones(int(keep.sum()), dtype=np.int64),
+                       (np.asarray(row_idx, dtype=np.int64)[keep], c_of[keep])),
+                      shape=(M, N))
+    C = (B @ B.T).toarray().astype(np.int64)
+    D = bounds.shape[0] - 1
+    out = []
+    for d in range(D):
+        lo, hi = int(bounds[d]), int(bounds[d + 1])
+        rows = np.nonzero(lonely[d])[0]
+        if rows.size == 0:
+            continue
+        Bd = B[:, lo:hi].tocsc()
+        for r0 in range(0, rows.size, 64):
+            part = rows[r0:r0 + 64]
+            Wt = np.asarray((sp.csr_matrix(C[part]) @ Bd).toarray(), dtype=np.int64)
+            cum = np.cumsum(Wt, axis=1)
+            for i, m in enumerate(part):
+                T = int(cum[i, -1])
+                if T == 0:
+                    if fallback_random:
+                        out.append((d, int(m), random_patch_col(seed, d, int(m), lo, hi - lo)))
+                    continue
+                r = (_philox_u64(seed, d, int(m)) * T) >> 64
+                out.append((d, int(m), lo + int(np.searchsorted(cum[i], r, side="right"))))
+    out.sort()
+    return np.asarray([(m, c) for _, m, c in out], dtype=np.int64).reshape(-1, 2)
 
 
 # --------------------------------------------------------------------------

@@ -28,6 +28,20 @@
  *     published definition (Salmon, Moraes, Dror, Shaw, "Parallel random
  *     numbers: as easy as 1, 2, 3", SC 2011), keyed by the caller's seed and
  *     counted by (row, block).
+ *   - ro_neighbor_list / ro_neighbor_patch_col: NeighborChecker (Algorithm 3)
+ *     for one lonely row m of block d.  The two lists are built exactly as
+ *     the algorithm builds them, as multisets: every row that shares a
+ *     non-zero column with m in another block, once per shared column
+ *     (row m itself included); then, for every list entry, every column of
+ *     block d where that row is non-zero.  Readings where the algorithm's
+ *     text is garbled: the second loop's row is the candidate the list entry
+ *     names (not the list position), and its columns run over block d's own
+ *     range.  The lists are built from the input A, before any insertion.
+ *     "Choose a random column from neighbourList" is a uniform draw over the
+ *     list's entries: the list is sorted ascending and entry
+ *     floor(x * T / 2^64) taken, x the 64-bit Philox word (m, d, 1, 0) and
+ *     T the list's length.  An empty list gives -1 (no column); Algorithm 4
+ *     (neighbourRandomChecker) then takes the RandomChecker column.
  */
 #include <math.h>
 #include <stdint.h>
@@ -69,6 +83,89 @@ int64_t ro_random_patch_col(uint64_t seed, int32_t d, int32_t m, int64_t lo,
     uint32_t out[4];
     ro_philox4x32_10(ctr, key, out);
     return lo + (int64_t)(((uint64_t)out[0] * (uint64_t)w) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 (NeighborChecker).  Growable arrays for the two lists. */
+typedef struct { int64_t* v; int64_t n, cap; } ro_list;
+
+static int ro_list_push(ro_list* l, int64_t x) {
+    if (l->n == l->cap) {
+        int64_t cap = l->cap ? 2 * l->cap : 64;
+        int64_t* v = (int64_t*)realloc(l->v, (size_t)cap * sizeof(int64_t));
+        if (!v) return -1;
+        l->v = v;
+        l->cap = cap;
+    }
+    l->v[l->n++] = x;
+    return 0;
+}
+
+static int ro_cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* High 64 bits of the 128-bit product a*b, from four 32x32 products. */
+uint64_t ro_mulhi64(uint64_t a, uint64_t b) {
+    uint64_t a0 = a & 0xffffffffu, a1 = a >> 32, b0 = b & 0xffffffffu, b1 = b >> 32;
+    uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+    uint64_t mid = (p00 >> 32) + (p01 & 0xffffffffu) + (p10 & 0xffffffffu);
+    return p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+/* The neighbour list of lonely row m in block d (dense row-major M x N A,
+ * D+1 column bounds), sorted ascending.  Returns its length and, when out is
+ * not NULL and cap allows, copies it there; -2 when memory ran out. */
+int64_t ro_neighbor_list(const double* A, int32_t M, int64_t N, const int64_t* bounds,
+                         int32_t D, int32_t d, int32_t m, int64_t* out, int64_t cap) {
+    ro_list cand = {0, 0, 0}, nbr = {0, 0, 0};
+    int64_t len = -2;
+    /* candidates: rows non-zero in a column of another block where m is */
+    for (int32_t d1 = 0; d1 < D; ++d1) {
+        if (d1 == d) continue;
+        for (int64_t n1 = bounds[d1]; n1 < bounds[d1 + 1]; ++n1) {
+            if (A[(int64_t)m * N + n1] == 0.0) continue;
+            for (int32_t m1 = 0; m1 < M; ++m1)
+                if (A[(int64_t)m1 * N + n1] != 0.0 && ro_list_push(&cand, m1)) goto done;
+        }
+    }
+    /* neighbours: columns of block d where a candidate is non-zero */
+    for (int64_t i = 0; i < cand.n; ++i) {
+        const int64_t c = cand.v[i];
+        for (int64_t n2 = bounds[d]; n2 < bounds[d + 1]; ++n2)
+            if (A[c * N + n2] != 0.0 && ro_list_push(&nbr, n2)) goto done;
+    }
+    if (nbr.n > 1) qsort(nbr.v, (size_t)nbr.n, sizeof(int64_t), ro_cmp_i64);
+    len = nbr.n;
+    if (out)
+        for (int64_t i = 0; i < len && i < cap; ++i) out[i] = nbr.v[i];
+done:
+    free(cand.v);
+    free(nbr.v);
+    return len;
+}
+
+/* NeighborChecker's column for lonely row m of block d: the list entry chosen
+ * by the draw described in the header, or -1 when the list is empty (-2 when
+ * memory ran out).  *list_len receives the list's length. */
+int64_t ro_neighbor_patch_col(const double* A, int32_t M, int64_t N, const int64_t* bounds,
+                              int32_t D, int32_t d, int32_t m, uint64_t seed,
+                              int64_t* list_len) {
+    int64_t len = ro_neighbor_list(A, M, N, bounds, D, d, m, NULL, 0);
+    if (list_len) *list_len = len;
+    if (len <= 0) return len == 0 ? -1 : -2;
+    int64_t* lst = (int64_t*)malloc((size_t)len * sizeof(int64_t));
+    if (!lst) return -2;
+    ro_neighbor_list(A, M, N, bounds, D, d, m, lst, len);
+    uint32_t ctr[4] = {(uint32_t)m, (uint32_t)d, 1u, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    ro_philox4x32_10(ctr, key, w);
+    const uint64_t x = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+    const int64_t col = lst[ro_mulhi64(x, (uint64_t)len)];
+    free(lst);
+    return col;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -26,6 +26,13 @@ MUTANTS = {
     "philox_key_bump": ("k1 += W1;", "k1 += W0;"),
     "lonely_bound": ("for (int64_t n = bounds[d]; n < bounds[d + 1]; ++n)",
                      "for (int64_t n = bounds[d]; n + 1 < bounds[d + 1]; ++n)"),
+    "neighbor_own_block": ("if (d1 == d) continue;", "if (d1 == d && 0) continue;"),
+    "neighbor_block_range": ("for (int64_t n2 = bounds[d]; n2 < bounds[d + 1]; ++n2)",
+                             "for (int64_t n2 = 0; n2 < bounds[d + 1]; ++n2)"),
+    "neighbor_unsorted": ("if (nbr.n > 1) qsort(", "if (nbr.n > 1 && 0) qsort("),
+    "neighbor_draw_words": ("(uint64_t)w[0] | ((uint64_t)w[1] << 32)",
+                            "(uint64_t)w[1] | ((uint64_t)w[0] << 32)"),
+    "neighbor_mulhi_carry": ("(p10 >> 32) + (mid >> 32);", "(p10 >> 32);"),
     "gram_transposed": ("s += A[(int64_t)i * N + n] * A[(int64_t)j * N + n];",
                         "s += A[(int64_t)i * N + n] * A[(int64_t)n * N + j];"),
 }
@@ -42,6 +49,11 @@ PINS = [
     pins.test_known_sigma_householder_products,
     pins.test_invariants_small_uniform,
     pins.test_transposed_operand_is_caught,
+    pins.test_neighbor_worked_example,
+    pins.test_neighbor_list_multiplicities_closed_form,
+    pins.test_neighbor_choice_against_closed_form,
+    pins.test_neighbor_draw_uniform_over_entries,
+    pins.test_neighbor_draw_product_exact,
 ]
 
 
@@ -63,7 +75,8 @@ def test_pins_catch_planted_mistake(name, tmp_path, monkeypatch):
     real = oracle._load()
     lib = ctypes.CDLL(so)
     for fn in ("ro_philox4x32_10", "ro_random_patch_col", "ro_lonely_dense",
-               "ro_gram_dense", "ro_svd_jacobi"):
+               "ro_gram_dense", "ro_svd_jacobi", "ro_neighbor_list",
+               "ro_neighbor_patch_col", "ro_mulhi64"):
         f = getattr(lib, fn)
         f.argtypes = getattr(real, fn).argtypes
         f.restype = getattr(real, fn).restype

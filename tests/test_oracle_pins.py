@@ -103,6 +103,196 @@ def test_lonely_sparse_equals_dense():
 
 
 # --------------------------------------------------------------------------
+# NeighborChecker (Algorithm 3) and neighbourRandomChecker (Algorithm 4)
+
+def _neighbor_example():
+    lines = [l.split() for l in open(golden_path("neighbor_example.txt"))
+             if l.strip() and not l.startswith("#")]
+    M, N = int(lines[0][0]), int(lines[0][1])
+    A = np.zeros((M, N))
+    for l in lines[1:]:
+        if l[0] == "blocks":
+            bounds = np.asarray([int(x) for x in l[1:]], dtype=np.int64)
+        elif l[0] == "lonely":
+            d, m = int(l[1]) - 1, int(l[2]) - 1
+        elif l[0] == "neighbours":
+            expect = [int(x) - 1 for x in l[1:]]
+        else:
+            A[int(l[0]) - 1, int(l[1]) - 1] = 1.0
+    return A, bounds, d, m, expect
+
+
+def _draw_index(seed, d, m, T):
+    """Entry of a T-long sorted list the draw selects: floor(x T / 2^64),
+    x = the Philox words (m, d, 1, 0) joined low word first (exact integers)."""
+    w = oracle.philox4x32_10([m, d, 1, 0], [seed & 0xFFFFFFFF, seed >> 32])
+    x = int(w[0]) | (int(w[1]) << 32)
+    return (x * T) >> 64
+
+
+def test_neighbor_worked_example():
+    A, bounds, d, m, expect = _neighbor_example()
+    lon, rne = oracle.lonely_dense(A, bounds)
+    assert lon[d, m] and rne[m]
+    assert oracle.neighbor_list(A, bounds, d, m).tolist() == expect
+    for seed in range(16):
+        col, T = oracle.neighbor_patch_col(A, bounds, d, m, seed)
+        assert T == len(expect)
+        assert col == expect[_draw_index(seed, d, m, T)]
+
+
+def test_neighbor_draw_product_exact():
+    """The list entry floor(x T / 2^64) is formed from four 32-bit partial
+    products; it equals the exact integer quotient for every operand size,
+    including carries out of the middle words."""
+    rng = np.random.default_rng(3)
+    cases = [(0, 0), (2**64 - 1, 2**64 - 1), (2**64 - 1, 1), (2**32, 2**32),
+             (2**63, 3), (0xFFFFFFFF, 0xFFFFFFFF), (2**64 - 1, 2**40 + 12345)]
+    cases += [(int(a), int(b)) for a, b in rng.integers(0, 2**63, size=(200, 2), dtype=np.uint64)]
+    cases += [(int(a) * 2 + 1, int(b) >> s) for (a, b), s in
+              zip(rng.integers(0, 2**63, size=(200, 2), dtype=np.uint64), range(200))]
+    for a, b in cases:
+        a &= 2**64 - 1
+        assert oracle.mulhi64(a, b) == (a * b) >> 64, (a, b)
+
+
+def _pattern_weights(A, bounds, d, m):
+    """Closed form of the neighbour list's multiplicities: column n of block d
+    appears sum_c C[m, c] B[c, n] times, B the 0/1 pattern of A and C the
+    co-occurrence counts B B^T over the columns outside block d."""
+    B = (A != 0).astype(np.int64)
+    lo, hi = int(bounds[d]), int(bounds[d + 1])
+    out = np.ones(B.shape[1], dtype=bool)
+    out[lo:hi] = False
+    C = B[:, out] @ B[:, out].T
+    return C[m] @ B[:, lo:hi]
+
+
+def _random_pattern(seed, M=9, N=40, density=0.12):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((M, N)) * (rng.random((M, N)) < density)
+    A[rng.random((M, N)) < 0.02] = 0.0
+    return A
+
+
+def test_neighbor_list_multiplicities_closed_form():
+    for seed in range(6):
+        A = _random_pattern(seed)
+        bounds = oracle.block_bounds(A.shape[1], 4)
+        for d in range(4):
+            lo = int(bounds[d])
+            for m in range(A.shape[0]):
+                w = _pattern_weights(A, bounds, d, m)
+                expect = np.repeat(np.arange(lo, lo + w.shape[0]), w)
+                got = oracle.neighbor_list(A, bounds, d, m)
+                assert got.tolist() == expect.tolist(), (seed, d, m)
+
+
+def test_neighbor_choice_against_closed_form():
+    for seed in range(4):
+        A = _random_pattern(seed + 10)
+        bounds = oracle.block_bounds(A.shape[1], 4)
+        lon, rne = oracle.lonely_dense(A, bounds)
+        lon &= rne[None, :]
+        for d, m in zip(*np.nonzero(lon)):
+            w = _pattern_weights(A, bounds, d, m)
+            col, T = oracle.neighbor_patch_col(A, bounds, int(d), int(m), 99 + seed)
+            assert T == int(w.sum())
+            if T == 0:
+                assert col == -1
+            else:
+                flat = np.repeat(np.arange(w.shape[0]), w) + int(bounds[d])
+                assert col == int(flat[_draw_index(99 + seed, int(d), int(m), T)])
+
+
+def test_neighbor_rule_membership_bruteforce():
+    """Every inserted entry obeys Algorithm 3's rule, checked by brute force:
+    row m is lonely in block d, the column lies in block d, and some row c
+    shares a non-zero column outside block d with m and is non-zero there."""
+    for seed in range(4):
+        A = _random_pattern(seed + 20, M=8, N=32, density=0.15)
+        bounds = oracle.block_bounds(32, 4)
+        lon, rne = oracle.lonely_dense(A, bounds)
+        lon &= rne[None, :]
+        P = oracle.neighbor_patches(A, bounds, lon, seed)
+        blk = np.searchsorted(bounds, P[:, 1], side="right") - 1
+        for (m, col), d in zip(P.tolist(), blk.tolist()):
+            assert lon[d, m]
+            lo, hi = int(bounds[d]), int(bounds[d + 1])
+            ok = False
+            for c in range(A.shape[0]):
+                if A[c, col] == 0:
+                    continue
+                for n1 in range(A.shape[1]):
+                    if not (lo <= n1 < hi) and A[m, n1] != 0 and A[c, n1] != 0:
+                        ok = True
+            assert ok, (m, col)
+
+
+def test_neighbor_empty_list_and_random_fallback():
+    A = np.zeros((3, 8))
+    A[0, 0] = 1.0; A[0, 5] = 1.0      # row 0 in blocks 0 and 1
+    A[1, 6] = 2.0                     # row 1 only in block 1, shares nothing
+    A[2, 1] = 1.0; A[2, 5] = 1.0      # row 2 shares column 5 with row 0
+    bounds = oracle.block_bounds(8, 2)
+    lon, rne = oracle.lonely_dense(A, bounds)
+    lon &= rne[None, :]
+    assert lon.astype(int).tolist() == [[0, 1, 0], [0, 0, 0]]
+    # row 1 in block 0: the only candidate is itself, empty in block 0
+    assert oracle.neighbor_list(A, bounds, 0, 1).tolist() == []
+    assert oracle.neighbor_patch_col(A, bounds, 0, 1, 5) == (-1, 0)
+    assert oracle.neighbor_patches(A, bounds, lon, 5).shape == (0, 2)
+    P = oracle.neighbor_patches(A, bounds, lon, 5, fallback_random=True)
+    assert P.tolist() == [[1, oracle.random_patch_col(5, 0, 1, 0, 4)]]
+
+
+def test_neighbor_single_distinct_column():
+    A = np.zeros((3, 8))
+    A[0, 2] = 1.0; A[0, 5] = 1.0      # row 0: column 2 of block 0, column 5
+    A[1, 5] = 1.0; A[1, 7] = 3.0      # row 1: lonely in block 0, shares column 5
+    A[2, 6] = 1.0
+    bounds = oracle.block_bounds(8, 2)
+    for seed in range(8):
+        assert oracle.neighbor_patch_col(A, bounds, 0, 1, seed) == (2, 1)
+
+
+def test_neighbor_draw_uniform_over_entries():
+    """The draw is uniform over the list's entries, not over its distinct
+    columns: a column listed twice is taken twice as often as one listed
+    once."""
+    A = np.zeros((4, 8))
+    A[:, 4] = 1.0                     # rows 0-3 share column 4 (block 1)
+    A[0, 0] = 1.0                     # row 0 lists column 0
+    A[1, 1] = 1.0; A[2, 1] = 1.0      # rows 1 and 2 both list column 1
+    bounds = oracle.block_bounds(8, 2)  # row 3 is lonely in block 0
+    assert oracle.neighbor_list(A, bounds, 0, 3).tolist() == [0, 1, 1]
+    cols = [oracle.neighbor_patch_col(A, bounds, 0, 3, s)[0] for s in range(4000)]
+    frac = np.mean(np.asarray(cols) == 1)
+    assert abs(frac - 2 / 3) < 4 * np.sqrt(2 / 9 / 4000)
+
+
+def _csc(A):
+    """CSC arrays of a dense matrix (stored entries = its non-zeros)."""
+    cols, rows = np.nonzero(A.T)
+    col_ptr = np.zeros(A.shape[1] + 1, dtype=np.int64)
+    np.add.at(col_ptr, cols + 1, 1)
+    return np.cumsum(col_ptr), rows.astype(np.int32), A[rows, cols]
+
+
+def test_neighbor_sparse_equals_dense():
+    for seed, fb in ((0, False), (1, True), (2, False), (3, True)):
+        A = _random_pattern(seed + 30, M=12, N=60, density=0.08)
+        bounds = oracle.block_bounds(60, 5)
+        lon, rne = oracle.lonely_dense(A, bounds)
+        lon &= rne[None, :]
+        P = oracle.neighbor_patches(A, bounds, lon, seed, fallback_random=fb)
+        col_ptr, row_idx, vals = _csc(A)
+        S = oracle.neighbor_patches_sparse(col_ptr, row_idx, vals, 12, bounds, lon, seed,
+                                           fallback_random=fb)
+        assert S.tolist() == P.tolist()
+
+
+# --------------------------------------------------------------------------
 # Eq. 2 block cross product and the proxy identity of Eqs. 2-3
 
 def test_gram_dense_against_matmul_and_sum():
