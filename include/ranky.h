@@ -67,8 +67,19 @@ typedef enum {
     SVD_RANKFIX_TRUNCATE = 0,        /* no insertion; drop numerically zero block
                                         directions (default) */
     SVD_RANKFIX_RANDOM = 1,          /* RandomChecker, Algorithm 2 */
-    SVD_RANKFIX_NEIGHBOR = 2,        /* NeighborChecker, Algorithm 3 (not built) */
-    SVD_RANKFIX_NEIGHBOR_RANDOM = 3  /* neighbourRandomChecker, Algorithm 4 (not built) */
+    SVD_RANKFIX_NEIGHBOR = 2,        /* NeighborChecker, Algorithm 3: for lonely row m
+                                        of block d, a column of block d drawn from the
+                                        multiset {n : rows c sharing a non-zero column
+                                        with m in another block, once per shared
+                                        column, and non-zero at (c, n)}; the 64-bit
+                                        Philox word of counter (m, d, 1, 0) selects
+                                        entry floor(x T / 2^64) of that list ordered
+                                        by column (T its length; T < 2^64 assumed).
+                                        All lists come from the input A.  An empty
+                                        list inserts nothing. */
+    SVD_RANKFIX_NEIGHBOR_RANDOM = 3  /* neighbourRandomChecker, Algorithm 4: as
+                                        NEIGHBOR, with the RANDOM column where the
+                                        neighbour list is empty */
 } svd_rankfix;
 
 typedef enum { SVD_VALUE_F32 = 0, SVD_VALUE_F64 = 1 } svd_value_type;
@@ -87,7 +98,7 @@ typedef struct {
     int32_t k;                       /* triplets returned, 0 = min(M, N) */
     int32_t precision;               /* svd_precision */
     int32_t rank_fix;                /* svd_rankfix */
-    uint64_t seed;                   /* RandomChecker key */
+    uint64_t seed;                   /* rank-fix key (Philox4x32-10) */
     double rank_tol;                 /* > 0: absolute tolerance on singular values;
                                         <= 0: a squared singular value (eigenvalue
                                         of the cross product) counts when it is
@@ -141,8 +152,8 @@ svd_status svd_plan_bytes(const svd_desc* desc, size_t* device_bytes_needed);
  *   d_V       float[N*k] (MIXED) or double[N*k] (FP64), row-major right
  *             vectors V = A'^T U S^-1; may be NULL with SVD_FLAG_SKIP_V
  *   d_rank    int32[1]             number of singular values above tolerance
- *   d_patches svd_patch[D*M]       RandomChecker insertions in (block, row)
- *             order (may be NULL when rank_fix is TRUNCATE)
+ *   d_patches svd_patch[D*M]       rank-fix insertions (value 1.0) in (block,
+ *             row) order (may be NULL when rank_fix is TRUNCATE)
  *   d_npatches int64[1]            number of insertions (may be NULL likewise)
  * Asynchronous; call svd_sync() (or synchronise the stream and call
  * svd_sync()) to read device-detected errors. */

@@ -33,6 +33,8 @@ struct svd_plan_s {
     int M = 0, Mp = 0, D = 0, k = 0;
     int64_t N = 0, nnz = 0;
     bool mixed = false, random = false;
+    bool neighbor = false;  // Algorithm 3 (or 4 with the RandomChecker fallback)
+    bool patched = false;   // any insertion mode
     double jac_tol = 0.0;
     int max_sweeps = 40, refine_iters = 1, merge_refine_iters = 3;
     std::vector<int64_t> bounds_h;
@@ -54,6 +56,10 @@ struct svd_plan_s {
     uint32_t* lonely = nullptr;
     PatchRec* patches = nullptr;
     int64_t* patch_ofs = nullptr;
+    uint32_t* lonely_any = nullptr;     // neighbour modes: rows lonely in some block
+    unsigned long long* cooc = nullptr; // neighbour modes: M x M row co-occurrence counts
+    PatchRec* slots = nullptr;          // neighbour modes: one per lonely node
+    int64_t* slot_ofs = nullptr;
     double* G64 = nullptr;
     double* Gw64 = nullptr;    // FP64: Jacobi working copy
     double* Vt64 = nullptr;    // FP64 eigenvector rows (FP64 solve, or converted FP32 + refined)
@@ -140,8 +146,6 @@ svd_status validate_desc(const svd_desc* d) {
     if (d->precision != SVD_PREC_FP64 && d->precision != SVD_PREC_MIXED) return SVD_ERR_INVALID_ARG;
     if (d->rank_fix < SVD_RANKFIX_TRUNCATE || d->rank_fix > SVD_RANKFIX_NEIGHBOR_RANDOM)
         return SVD_ERR_INVALID_ARG;
-    if (d->rank_fix == SVD_RANKFIX_NEIGHBOR || d->rank_fix == SVD_RANKFIX_NEIGHBOR_RANDOM)
-        return SVD_ERR_UNSUPPORTED;
     if (d->k < 0) return SVD_ERR_INVALID_ARG;
     const int64_t kmax = std::min<int64_t>(d->M, d->N);
     if (d->k > kmax) return SVD_ERR_INVALID_ARG;
@@ -168,6 +172,12 @@ void carve(svd_plan_s* p, Carver& c) {
     p->lonely = c.take<uint32_t>((size_t)D * p->W);
     p->patches = c.take<PatchRec>((size_t)D * M);
     p->patch_ofs = c.take<int64_t>(D + 1);
+    if (p->neighbor) {
+        p->lonely_any = c.take<uint32_t>(p->W);
+        p->cooc = c.take<unsigned long long>((size_t)M * M);
+        p->slots = c.take<PatchRec>((size_t)D * M);
+        p->slot_ofs = c.take<int64_t>(D + 1);
+    }
     p->G64 = c.take<double>((size_t)D * mm);
     p->Vt64 = c.take<double>((size_t)D * mm);
     if (p->mixed) {
@@ -233,6 +243,8 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
     p->k = d->k > 0 ? d->k : (int)std::min<int64_t>(d->M, d->N);
     p->mixed = d->precision == SVD_PREC_MIXED;
     p->random = d->rank_fix == SVD_RANKFIX_RANDOM;
+    p->neighbor = d->rank_fix == SVD_RANKFIX_NEIGHBOR || d->rank_fix == SVD_RANKFIX_NEIGHBOR_RANDOM;
+    p->patched = p->random || p->neighbor;
     p->use_oz = p->mixed && !(d->flags & SVD_FLAG_FP64_PRODUCTS);
     p->Mp = jacobi_pad(d->M);
     p->W = (d->M + 31) / 32;
@@ -339,13 +351,25 @@ svd_status phase_pre(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
     CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
     LAUNCH(p, 1, launch_occupancy(io.col_ptr, io.row_idx, io.vals, vt, M, p->nchunks,
                                   p->chunk_block, p->chunk_lo, p->chunk_hi, p->occ, s));
-    LAUNCH(p, 1, launch_lonely_patches(p->occ, D, M, p->bounds_d, p->random ? 1 : 0, p->d.seed,
-                                       p->row_ne, p->lonely, p->patches, p->patch_ofs,
-                                       reinterpret_cast<PatchRec*>(io.patches), io.npatches, s));
+    PatchRec* ext = reinterpret_cast<PatchRec*>(io.patches);
+    if (!p->neighbor) {
+        LAUNCH(p, 1, launch_lonely_patches(p->occ, D, M, p->bounds_d, p->random ? 1 : 0,
+                                           p->d.seed, p->row_ne, p->lonely, p->patches,
+                                           p->patch_ofs, ext, io.npatches, nullptr, s));
+    } else {
+        LAUNCH(p, 1, launch_lonely_patches(p->occ, D, M, p->bounds_d, 2, p->d.seed, p->row_ne,
+                                           p->lonely, p->slots, p->slot_ofs, nullptr, nullptr,
+                                           p->lonely_any, s));
+        LAUNCH(p, 3, launch_neighbor_patches(io.col_ptr, io.row_idx, io.vals, vt, M, p->N, D,
+                                             p->bounds_d, p->lonely_any, p->cooc,
+                                             p->d.rank_fix == SVD_RANKFIX_NEIGHBOR_RANDOM,
+                                             p->d.seed, p->slots, p->slot_ofs, p->patches,
+                                             p->patch_ofs, ext, io.npatches, s));
+    }
     mark(p, 1, s);
     LAUNCH(p, 1, launch_gram(io.col_ptr, io.row_idx, io.vals, vt, Mp, p->nchunks, p->chunk_block,
                              p->chunk_lo, p->chunk_hi, p->G64, s));
-    if (p->random)
+    if (p->patched)
         LAUNCH(p, 1, launch_gram_patches(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->patches,
                                          p->patch_ofs, D * M, p->G64, s));
     LAUNCH(p, 1, launch_symmetrize(p->G64, D, Mp, s));
@@ -403,7 +427,7 @@ svd_status phase_mid(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         // (measured: one scatter update costs about as much as 100 dense
         // multiply-adds there), on the FP64 pipes otherwise (about 8).
         const double dense_per_nnz = p->use_oz ? 100.0 : 8.0;
-        const bool sparse = !p->random && !(p->d.flags & SVD_FLAG_DENSE_REFINE) &&
+        const bool sparse = !p->patched && !(p->d.flags & SVD_FLAG_DENSE_REFINE) &&
                             dense_per_nnz * (double)p->nnz < (double)D * Mp * (double)Mp;
         const SparseBlocks sb{io.col_ptr, io.row_idx, io.vals, p->d.value_type, p->nchunks,
                               p->chunk_block, p->chunk_lo, p->chunk_hi};
@@ -487,13 +511,13 @@ svd_status phase_post(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         if (p->mixed) {
             LAUNCH(p, 1, launch_spmm<float>(io.col_ptr, io.row_idx, io.vals, vt, p->N, p->k, p->W32,
                                             static_cast<float*>(io.V), s));
-            if (p->random)
+            if (p->patched)
                 LAUNCH(p, 1, launch_spmm_patches<float>(p->patches, p->patch_ofs + D, D * M, p->k,
                                                         p->W32, static_cast<float*>(io.V), s));
         } else {
             LAUNCH(p, 1, launch_spmm<double>(io.col_ptr, io.row_idx, io.vals, vt, p->N, p->k,
                                              p->W64, static_cast<double*>(io.V), s));
-            if (p->random)
+            if (p->patched)
                 LAUNCH(p, 1, launch_spmm_patches<double>(p->patches, p->patch_ofs + D, D * M, p->k,
                                                          p->W64, static_cast<double*>(io.V), s));
         }
@@ -657,9 +681,9 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
     // A page-locked V buffer is addressable from the device (unified
     // addressing; on this part over the chip-to-chip link): the SpMM then
     // streams V straight into it and the 2 GB copy disappears.  Not with
-    // RandomChecker insertions, whose V correction uses atomic adds.
+    // rank-fix insertions, whose V correction uses atomic adds.
     void* dV_direct = nullptr;
-    if (want_v && !p->random) {
+    if (want_v && !p->patched) {
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, h_V) == cudaSuccess && at.type == cudaMemoryTypeHost &&
             at.devicePointer)

@@ -19,11 +19,24 @@ cudaError_t launch_occupancy(const int64_t* col_ptr, const int32_t* row_idx, con
                              const int64_t* chunk_col_lo, const int64_t* chunk_col_hi,
                              uint32_t* occ, cudaStream_t s);
 // occ: D x W words (W = ceil(M/32)).  Writes row_ne (W words), lonely (D x W),
-// and, when random != 0, patches in (block, row) order with per-block offsets.
+// and, by mode, nothing more (0), RandomChecker patches (1) or one slot with
+// col = -1 per lonely node (2), in (block, row) order with per-block offsets;
+// lonely_any (W words, may be null) = rows lonely in some block.
 cudaError_t launch_lonely_patches(const uint32_t* occ, int D, int M, const int64_t* bounds,
-                                  int random, uint64_t seed, uint32_t* row_ne, uint32_t* lonely,
+                                  int mode, uint64_t seed, uint32_t* row_ne, uint32_t* lonely,
                                   PatchRec* patches, int64_t* patch_ofs, PatchRec* ext_patches,
-                                  int64_t* ext_npatches, cudaStream_t s);
+                                  int64_t* ext_npatches, uint32_t* lonely_any, cudaStream_t s);
+// Algorithms 3-4 over the slots of mode 2: row co-occurrence counts (cooc,
+// M x M, cleared here), a column per slot (or none; RandomChecker's when
+// fallback), then the filled slots compacted into patches / patch_ofs (and
+// the caller's copy).  Three kernels.
+cudaError_t launch_neighbor_patches(const int64_t* col_ptr, const int32_t* row_idx,
+                                    const void* vals, int value_type, int M, int64_t N, int D,
+                                    const int64_t* bounds, const uint32_t* lonely_any,
+                                    unsigned long long* cooc, int fallback, uint64_t seed,
+                                    PatchRec* slots, const int64_t* slot_ofs, PatchRec* patches,
+                                    int64_t* patch_ofs, PatchRec* ext_patches,
+                                    int64_t* ext_npatches, cudaStream_t s);
 
 // ---- gram.cu: Eq. 2 block cross products --------------------------------------
 // G: D x Mp x Mp FP64 (upper triangle accumulated; must be zero on entry).

@@ -465,9 +465,9 @@ svd_status svd_server_submit(svd_server_t s, const svd_request* req, uint64_t* t
     if (!req->h_V) r->desc.flags |= SVD_FLAG_SKIP_V;   // no V wanted: none computed
     r->plan_bytes = plan_bytes;
     // a page-locked V buffer is written in place by the device (no staging
-    // buffer in the pool, no copy); not with RandomChecker insertions, whose V
+    // buffer in the pool, no copy); not with rank-fix insertions, whose V
     // correction uses atomic adds
-    if (req->h_V && !(r->desc.flags & SVD_FLAG_SKIP_V) && r->desc.rank_fix != SVD_RANKFIX_RANDOM) {
+    if (req->h_V && !(r->desc.flags & SVD_FLAG_SKIP_V) && r->desc.rank_fix == SVD_RANKFIX_TRUNCATE) {
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, req->h_V) == cudaSuccess && at.type == cudaMemoryTypeHost &&
             at.devicePointer)

@@ -24,6 +24,13 @@ Workloads (sizes as named by the workload, not by the paper, whose own
                          ``scale`` shrinks N (and the non-zero count) for tests.
 * ``batch_mix``          independent matrices: M ~ U{32..256}, N ~ logU[1e3,2e5],
                          density ~ logU[0.005,0.05], N(0,1) values.
+* ``neighbor_mix``       rank-fix pattern for the neighbour checkers: M=96,
+                         N=3001, 7 lognormal(0.5) block widths; rows 0-47 spread
+                         over all blocks (Bernoulli(0.03)), rows 48-92 living in
+                         one block each (two entries; the even ones next to a
+                         spread row, the odd ones in columns of their own), four
+                         columns of 40 spread rows, 24 stored zeros (some beside
+                         the lone rows), rows 93-95 empty.
 * ``arrival_stream``     Poisson arrivals of batch_mix-shaped requests with 5%
                          zipf_wide-shaped ones.
 """
@@ -258,6 +265,48 @@ def batch_mix(count: int = 2000, seed: int = SEED_BASE + 4, dtype=np.float32):
     subseeds = rng.integers(1 << 62, size=count)
     return [batch_matrix(M, N, rho, int(ss), dtype) for (M, N, rho), ss in
             zip(shapes, subseeds)]
+
+
+def neighbor_mix(seed: int = SEED_BASE + 6, dtype=np.float64) -> CscCase:
+    """Pattern that exercises both outcomes of the neighbour rank fix (see
+    the module docstring): lonely rows with neighbours, lonely rows whose
+    neighbour lists are empty, long columns and stored zeros."""
+    M, N, D = 96, 3001, 7
+    rng = np.random.default_rng(seed)
+    widths = lognormal_widths(rng, N, D, 0.5)
+    bounds = np.concatenate([[0], np.cumsum(widths)])
+    V = np.zeros((M, N))
+    spread = rng.random((48, N)) < 0.03
+    V[:48][spread] = rng.standard_normal(int(spread.sum()))
+    for c in rng.choice(N, size=4, replace=False):
+        rows = rng.choice(48, size=40, replace=False)
+        V[rows, c] = rng.standard_normal(40)
+    used = set()
+    for m in range(48, 93):
+        d = int(rng.integers(D))
+        lo, hi = int(bounds[d]), int(bounds[d + 1])
+        if m % 2 == 0:
+            cols = [c for c in rng.permutation(np.arange(lo, hi))
+                    if V[:48, c].any() and c not in used][:2]
+        else:
+            cols = [c for c in rng.permutation(np.arange(lo, hi))
+                    if not V[:, c].any() and c not in used][:2]
+        for c in cols:
+            used.add(int(c))
+            V[m, c] = rng.standard_normal()
+    stored = V != 0
+    # stored zeros: next to lone rows (they must not make neighbours) and at random
+    lone_cols = [c for c in sorted(used) if not V[:48, c].any()]
+    for c in rng.choice(lone_cols, size=min(12, len(lone_cols)), replace=False):
+        stored[int(rng.integers(48)), c] = True
+    for _ in range(12):
+        stored[int(rng.integers(48)), int(rng.integers(N))] = True
+    cols, rows = np.nonzero(stored.T)
+    col_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(cols, minlength=N), out=col_ptr[1:])
+    vals = V[rows, cols].astype(dtype)
+    return CscCase("neighbor_mix", M, N, col_ptr, rows.astype(np.int32), vals, D,
+                   widths.astype(np.int64), k=M, seed=seed)
 
 
 def random_dense_csc(rng: np.random.Generator, M: int, N: int, density: float,

@@ -96,7 +96,10 @@ def test_plan_bytes_validation(lib):
     for kw in bad:
         assert _bytes(lib, **kw)[0] == 1, kw
     assert _bytes(lib, **{**ok, "M": 1025})[0] == 8
-    assert _bytes(lib, **{**ok, "rank_fix": "neighbor"})[0] == 8
+    # the neighbour modes carry their own workspace (M x M counts, one slot per lonely node)
+    st3, n3 = _bytes(lib, **{**ok, "rank_fix": "neighbor"})
+    assert st3 == 0 and n3 > n
+    assert _bytes(lib, **{**ok, "rank_fix": "neighbor_random"}) == (0, n3)
     assert _bytes(lib, **{**ok, "bounds": [0, 1, 2, 3, 4096]})[0] == 0
 
 

@@ -54,16 +54,19 @@ def run_case(case, precision, rank_fix="truncate", seed=1234, vdtype=None, bound
     return res
 
 
-def oracle_for(case, res):
-    p = res["patches"] if len(res["patches"]) else None
+def oracle_for(case, res, patches=None):
+    p = res["patches"] if patches is None else patches
+    p = p if len(p) else None
     s, U, V, sweeps = oracle.svd_csc(case.col_ptr, case.row_idx, res["vals64"], case.M, case.N, p)
     assert sweeps > 0
     return s, U, V
 
 
-def check_against_oracle(case, res, precision, k=None):
+def check_against_oracle(case, res, precision, k=None, patches=None):
+    """patches: the insertions the oracle computed for this case (the CUDA
+    path's own list is only compared with it, never fed to the oracle)."""
     rel_tol, abs_tol = TOL[precision]
-    s_ref, U_ref, V_ref = oracle_for(case, res)
+    s_ref, U_ref, V_ref = oracle_for(case, res, patches)
     kk = len(res["sigma"]) if k is None else k
     sigma_check(res["sigma"], s_ref[:kk], rel_tol, abs_tol)
     sub_tol = 1e-4
@@ -150,9 +153,80 @@ def test_small_lonely_random_checker(precision):
     # each insertion lies in the lonely row's block (Algorithm 2)
     for (m, col), d in zip(res["patches"], res["patch_blocks"]):
         assert b[d] <= col < b[d + 1] and fix[d, m]
-    check_against_oracle(case, res, precision)
+    check_against_oracle(case, res, precision, patches=expect)
     # after the fix every block has full row rank
     assert (res["plan"].query(rk.Q_BLOCK_RANKS) == case.M).all()
+
+
+# --------------------------------------------------------------------------
+# NeighborChecker (Algorithm 3) and neighbourRandomChecker (Algorithm 4)
+
+def _case_bounds(case):
+    if case.widths is not None:
+        return np.concatenate([[0], np.cumsum(case.widths)]).astype(np.int64)
+    return oracle.block_bounds(case.N, case.num_blocks)
+
+
+@pytest.mark.parametrize("precision,vdtype", [("fp64", None), ("mixed", None),
+                                              ("mixed", np.float32)])
+@pytest.mark.parametrize("mode", ["neighbor", "neighbor_random"])
+def test_neighbor_checkers(precision, vdtype, mode):
+    """Both outcomes of the neighbour fix on one matrix: lonely rows with a
+    neighbour list, lonely rows without one (no insertion, or RandomChecker's
+    column), long columns, stored zeros, ragged block widths."""
+    case = synth.neighbor_mix()
+    seed = 0x5EED00012345
+    res = run_case(case, precision, mode, seed=seed, vdtype=vdtype)
+    b = _case_bounds(case)
+    A = oracle.densify(case.col_ptr, case.row_idx, case.vals, case.M, case.N)
+    lon, rne = oracle.lonely_dense(A, b)
+    fix = lon & rne[None, :]
+    expect = oracle.neighbor_patches(A, b, fix, seed, fallback_random=(mode == "neighbor_random"))
+    assert res["patches"].tolist() == expect.tolist()
+    if mode == "neighbor":
+        assert 0 < len(expect) < int(fix.sum())
+    else:
+        assert len(expect) == int(fix.sum())
+    blocks = np.searchsorted(b, expect[:, 1], side="right") - 1
+    assert res["patch_blocks"].tolist() == blocks.tolist()
+    check_against_oracle(case, res, precision, patches=expect)
+
+
+def test_neighbor_checker_small_lonely():
+    """Every lonely row of small_lonely has neighbours: eight insertions,
+    each block at full row rank afterwards."""
+    case = synth.small_lonely()
+    seed = 31337
+    res = run_case(case, "mixed", "neighbor", seed=seed)
+    b = oracle.block_bounds(case.N, case.num_blocks)
+    A = oracle.densify(case.col_ptr, case.row_idx, case.vals, case.M, case.N)
+    lon, rne = oracle.lonely_dense(A, b)
+    expect = oracle.neighbor_patches(A, b, lon & rne[None, :], seed)
+    assert len(expect) == 8
+    assert res["patches"].tolist() == expect.tolist()
+    check_against_oracle(case, res, "mixed", patches=expect)
+    assert (res["plan"].query(rk.Q_BLOCK_RANKS) == case.M).all()
+
+
+def test_neighbor_random_zipf_scaled():
+    """zipf_wide's shape at a quarter of its columns (512 x 250000, 64
+    blocks of 3906, ~750 lonely nodes): every insertion bit for bit against the
+    closed-form evaluation of the neighbour lists, the leading triplets by
+    their residuals against A'."""
+    case = synth.zipf_wide(M=512, N=250_000, D=64, target_nnz=128_000)
+    seed = 2009
+    res = run_case(case, "mixed", "neighbor_random", seed=seed)
+    b = oracle.block_bounds(case.N, case.num_blocks)
+    lon, rne = oracle.lonely_sparse(case.col_ptr, case.row_idx, case.vals, case.M, b)
+    fix = lon & rne[None, :]
+    expect = oracle.neighbor_patches_sparse(case.col_ptr, case.row_idx, case.vals, case.M, b,
+                                            fix, seed, fallback_random=True)
+    assert len(expect) == int(fix.sum()) > 0
+    assert res["patches"].tolist() == expect.tolist()
+    k = 8
+    r = oracle.residuals(case.col_ptr, case.row_idx, res["vals64"], case.M, res["sigma"][:k],
+                         res["U"][:, :k], res["V"][:, :k], patches=expect)
+    assert (r <= 1e-4 * res["sigma"][0]).all(), r
 
 
 # --------------------------------------------------------------------------
