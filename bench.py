@@ -417,19 +417,24 @@ def run_single_case(args):
         c = synth.small_uniform().with_values(np.float32)
         bounds, k = None, 0
     p = rk.Plan(c.M, c.N, c.nnz, c.num_blocks, value_type="f32", precision=args.precision,
-                bounds=bounds, k=k, flags=rk.FLAG_TIMING)
-    o = rk.alloc_outputs(p, device=dev, with_patches=False)
+                bounds=bounds, k=k, flags=rk.FLAG_TIMING, rank_fix=args.rank_fix,
+                seed=args.seed)
+    o = rk.alloc_outputs(p, device=dev, with_patches=True)
     cp, ri, va = (torch.from_numpy(c.col_ptr).to(dev), torch.from_numpy(c.row_idx).to(dev),
                   torch.from_numpy(c.vals).to(dev))
     stream = torch.cuda.current_stream(dev)
+    def step():
+        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"], o["patches"], o["npatches"],
+              stream=stream)
+
     for _ in range(max(1, args.warmup)):
-        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"], stream=stream)
+        step()
     p.sync()
     p.query(rk.Q_STAGE_TOTAL)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        p.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"], stream=stream)
+        step()
     ev1.record(stream)
     p.sync()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -437,7 +442,9 @@ def run_single_case(args):
     line = {"metric": "SVD/s (" + args.workload + ", " + args.precision + ")",
             "value": 1e3 / ms, "unit": "SVD/s", "ms_per_step": ms, "steps": args.steps,
             "config": {"workload": f"{c.name} M={c.M} N={c.N} nnz={c.nnz} D={c.num_blocks} "
-                                   f"k={p.k}", "precision": args.precision},
+                                   f"k={p.k}", "precision": args.precision,
+                       "rank_fix": args.rank_fix, "insertions": int(o["npatches"].item()),
+                       "lonely_nodes": int(p.query(rk.Q_LONELY).sum())},
             "stage_ms": {n: float(totals[i] / max(totals[-1], 1)) for i, n in enumerate(rk.STAGES)},
             "sweeps": p.query(rk.Q_SWEEPS).tolist()[-1], "rank": int(o["rank"].item()),
             "sigma_head": o["sigma"][:3].cpu().tolist()}
@@ -467,6 +474,10 @@ def main():
     ap.add_argument("--grace", type=float, default=15.0,
                     help="serve: seconds after the last arrival before queued requests are dropped")
     ap.add_argument("--large-cols", type=int, default=8_000_000, help="large: columns")
+    ap.add_argument("--rank-fix", default="truncate",
+                    choices=["truncate", "random", "neighbor", "neighbor_random"],
+                    help="large/small: rank fix (Algorithms 2-4); the headline is truncate")
+    ap.add_argument("--seed", type=int, default=1, help="rank-fix key")
     args = ap.parse_args()
 
     if args.impl == "reference":
