@@ -400,8 +400,10 @@ def run_serve(args):
 
 
 def run_single_case(args):
-    """One large (1024 x 8e6, ~80M nnz, 256 lognormal blocks, k=100) or small
-    (64 x 4096, 4 blocks) SVD, timed like the headline."""
+    """One large (1024 x 8e6, ~80M nnz, 256 lognormal blocks, k=100), small
+    (64 x 4096, 4 blocks) or tall (zipf_wide transposed: 1e6 x 512, 64 row
+    blocks, through the tall entry, whose device transpose is inside the
+    step) SVD, timed like the headline."""
     import torch
 
     import paper_2009_09767_gb300 as rk
@@ -409,15 +411,30 @@ def run_single_case(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    flags = rk.FLAG_TIMING
     if args.workload == "large":
         c = synth.large_skewed(N=args.large_cols, D=max(1, int(round(256 * args.large_cols / 8e6))))
         bounds = np.concatenate([[0], np.cumsum(c.widths)]).astype(np.int64)
         k = 100
+    elif args.workload == "tall":
+        import dataclasses
+
+        import scipy.sparse as sp
+        z = synth.zipf_wide(N=args.cols)
+        # the CSC of the tall A = zipf_wide^T is zipf_wide's CSR (host set-up)
+        At = sp.csc_matrix((z.vals, z.row_idx, z.col_ptr), shape=(z.M, z.N)).T.tocsc()
+        At.sort_indices()
+        c = dataclasses.replace(z, name="zipf_wide^T", M=z.N, N=z.M,
+                                col_ptr=At.indptr.astype(np.int64),
+                                row_idx=At.indices.astype(np.int32),
+                                vals=At.data.astype(np.float32))
+        bounds, k = None, 0
+        flags |= rk.FLAG_TALL
     else:
         c = synth.small_uniform().with_values(np.float32)
         bounds, k = None, 0
     p = rk.Plan(c.M, c.N, c.nnz, c.num_blocks, value_type="f32", precision=args.precision,
-                bounds=bounds, k=k, flags=rk.FLAG_TIMING, rank_fix=args.rank_fix,
+                bounds=bounds, k=k, flags=flags, rank_fix=args.rank_fix,
                 seed=args.seed)
     o = rk.alloc_outputs(p, device=dev, with_patches=True)
     cp, ri, va = (torch.from_numpy(c.col_ptr).to(dev), torch.from_numpy(c.row_idx).to(dev),
@@ -465,9 +482,10 @@ def main():
     ap.add_argument("--cols", type=int, default=1_000_000,
                     help="columns of the zipf_wide matrix (smaller cases for profiling)")
     ap.add_argument("--workload", default="zipf_wide",
-                    choices=["zipf_wide", "batch", "serve", "large", "small"],
+                    choices=["zipf_wide", "batch", "serve", "large", "small", "tall"],
                     help="zipf_wide (default, the headline), batch (many matrices in one "
-                         "pass), serve (Poisson arrivals), large (1024 x 8e6), small (64 x 4096)")
+                         "pass), serve (Poisson arrivals), large (1024 x 8e6), small (64 x 4096), "
+                         "tall (zipf_wide transposed, row blocks)")
     ap.add_argument("--count", type=int, default=2000, help="batch: matrices")
     ap.add_argument("--rates", default="50,100,200,400", help="serve: arrival rates (req/s)")
     ap.add_argument("--duration", type=float, default=8.0, help="serve: seconds per rate")
@@ -485,7 +503,7 @@ def main():
         return
     if args.workload != "zipf_wide":
         {"batch": run_batch, "serve": run_serve, "large": run_single_case,
-         "small": run_single_case}[args.workload](args)
+         "small": run_single_case, "tall": run_single_case}[args.workload](args)
         return
 
     import torch

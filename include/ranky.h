@@ -86,8 +86,8 @@ typedef enum { SVD_VALUE_F32 = 0, SVD_VALUE_F64 = 1 } svd_value_type;
 
 /* Problem description (section III: A is M x N, split into D column blocks). */
 typedef struct {
-    int32_t M;                       /* rows, 1 .. 1024 */
-    int64_t N;                       /* columns, >= 1 */
+    int32_t M;                       /* rows, 1 .. 1024 (any >= 1 with SVD_FLAG_TALL) */
+    int64_t N;                       /* columns, >= 1 (<= 1024 with SVD_FLAG_TALL) */
     int64_t nnz;                     /* stored entries, >= 0 */
     int32_t value_type;              /* svd_value_type of the values array */
     int32_t num_blocks;              /* D, 1 .. N */
@@ -122,6 +122,23 @@ typedef struct {
                                  P P^T with FP64 arithmetic instead of exact 8-bit
                                  slices on the bf16 tensor cores (for testing and
                                  timing) */
+#define SVD_FLAG_TALL 32       /* tall-and-skinny A: M rows (any, >= 1) and N <= 1024
+                                 columns, split into num_blocks ROW blocks (the row-block
+                                 form of section II); block_col_bounds then holds D+1
+                                 row boundaries ending at M.  The CSC still describes A.
+                                 The plan transposes it on the device and runs the
+                                 column-block path on A^T.  A^T's column blocks are A's
+                                 row blocks.  The outputs swap layouts:
+                                   d_U  float[M*k] (MIXED) or double[M*k] (FP64),
+                                        row-major left vectors U = A' V S^-1 (pass the
+                                        pointer cast to double*); SVD_FLAG_SKIP_V skips
+                                        them (the long side), d_U may then be NULL;
+                                   d_V  double[N*k] column-major right vectors.
+                                 Lonely nodes, insertions and svd_query results are
+                                 those of A^T. A lonely node is a column of A with no
+                                 entry inside a row block. An insertion's row is a
+                                 column of A and its col is a row of A. Batches and the
+                                 server return SVD_ERR_UNSUPPORTED for tall plans. */
 
 /* One RandomChecker insertion: A'[row, col] = 1.0 (Algorithm 2). */
 typedef struct {

@@ -35,6 +35,18 @@ What each function follows:
   (B B^T)[m, :] B[:, n] times in row m's neighbour list.  Used where a dense
   copy does not fit; pinned against the literal lists.
 * ``gram_dense``: Eq. 2's block cross product by plain summation.
+* ``svd_tall``: the row-block (tall-and-skinny) form of section II.  For a
+  tall A the method splits the rows into blocks; A^T is then short and fat
+  with those blocks as its column blocks, so the method reaches the SVD of
+  A'^T = V S U^T, whose factors are A' = U S V^T with the roles exchanged.
+  Insertions are given in A^T's coordinates (row = column of A).
+* ``svd_gram_01``: the SVD of A' for matrices with small integer entries (the
+  0/1 patterns of the paper's job-candidate data).  Section III reads the
+  singular values as the square roots of the eigenvalues of A A^*; for an
+  integer A' the cross product A'A'^T is formed exactly in FP64, so the only
+  rounding is the symmetric eigensolver's (LAPACK, through numpy).  Used as
+  the truth where the dense Jacobi SVD would take minutes; pinned against
+  ``svd_csc``.
 * ``residuals``: a-posteriori residual bounds max(|A v - s u|, |A^T u - s v|)
   for triplets of matrices too large to densify; each bounds the distance
   from s to a true singular value.
@@ -370,6 +382,54 @@ def svd_csc(col_ptr, row_idx, vals, M: int, N: int, patches=None,
     V = np.zeros((N, M), dtype=np.float64)
     V[cols] = Vc
     return s, U, V, sweeps
+
+
+def svd_tall(col_ptr, row_idx, vals, M: int, N: int, patches_t=None,
+             max_sweeps: int = 100, tol: float = 1e-15):
+    """SVD of a tall A' (M x N CSC, patches_t = insertions (column of A, row
+    of A) in A^T's coordinates): the Jacobi SVD of A'^T with U and V
+    exchanged.  Returns (sigma[N], U[M, N], V[N, N], sweeps)."""
+    At = np.ascontiguousarray(densify(col_ptr, row_idx, vals, M, N).T)
+    if patches_t is not None and len(patches_t):
+        p = np.asarray(patches_t, dtype=np.int64).reshape(-1, 2)
+        np.add.at(At, (p[:, 0], p[:, 1]), 1.0)
+    s, Ut, Vt, sweeps = svd_dense(At, max_sweeps, tol)
+    return s, Vt, Ut, sweeps
+
+
+def svd_gram_01(col_ptr, row_idx, vals, M: int, N: int, patches=None, return_gram=False):
+    """sigma (descending) and U (M x M) of A' = A + patches for an A with
+    integer entries, from the exactly formed cross product A'A'^T (returned
+    third with return_gram).  Raises ValueError when the entries are not
+    integers or the products could leave the exactly representable range
+    (2^53)."""
+    import scipy.sparse as sp
+
+    col_ptr = np.asarray(col_ptr, dtype=np.int64)
+    v = np.asarray(vals, dtype=np.float64)
+    if not np.all(v == np.round(v)):
+        raise ValueError("svd_gram_01 needs integer entries")
+    c_of = np.repeat(np.arange(N, dtype=np.int64), np.diff(col_ptr))
+    r = np.asarray(row_idx, dtype=np.int64)
+    if patches is not None and len(patches):
+        p = np.asarray(patches, dtype=np.int64).reshape(-1, 2)
+        r = np.concatenate([r, p[:, 0]])
+        c_of = np.concatenate([c_of, p[:, 1]])
+        v = np.concatenate([v, np.ones(p.shape[0])])
+    A = sp.csr_matrix((v.astype(np.int64), (r, c_of)), shape=(M, N))
+    G = (A @ A.T).toarray()
+    if np.abs(G).max() >= 2**53 / max(M, 1):
+        raise ValueError("cross product outside the exact FP64 integers")
+    lam, U = np.linalg.eigh(G.astype(np.float64))
+    order = np.argsort(-lam, kind="stable")
+    lam, U = lam[order], U[:, order]
+    sigma = np.sqrt(np.maximum(lam, 0.0))
+    # sign rule of the product: the largest-magnitude entry of each u is positive
+    arg = np.argmax(np.abs(U), axis=0)
+    U = U * np.where(U[arg, np.arange(M)] < 0, -1.0, 1.0)[None, :]
+    if return_gram:
+        return sigma, U, G.astype(np.float64)
+    return sigma, U
 
 
 # --------------------------------------------------------------------------

@@ -35,6 +35,7 @@ FLAG_SKIP_V = 2
 FLAG_TIMING = 4
 FLAG_DENSE_REFINE = 8
 FLAG_FP64_PRODUCTS = 16
+FLAG_TALL = 32
 STAGES = ["partition", "gram", "block_jacobi", "block_refine", "sort_proxy", "merge_gram",
           "merge_eig", "finalize", "spmm"]
 
@@ -168,6 +169,9 @@ class Plan:
         self.value_type = kw.get("value_type", "f32")
         k = int(kw.get("k", 0))
         self.k = k if k > 0 else min(self.M, self.N)
+        # tall plans (FLAG_TALL): the problem solved is A^T; its short side is N
+        self.tall = bool(int(kw.get("flags", 0)) & FLAG_TALL)
+        self.Ms = self.N if self.tall else self.M
         d, keep = make_desc(M, N, nnz, num_blocks, **kw)
         h = ctypes.c_void_p()
         nbytes = ctypes.c_size_t(0)
@@ -203,7 +207,7 @@ class Plan:
 
     def query(self, what: int, index: int = 0):
         lib = load_library()
-        D, M = self.D, self.M
+        D, M = self.D, self.Ms
         if what == Q_BLOCK_BOUNDS:
             out = np.zeros(D + 1, np.int64)
         elif what == Q_LONELY:
@@ -247,17 +251,25 @@ class Plan:
 
 
 def alloc_outputs(plan: Plan, device="cuda", with_patches=True):
-    """Device output tensors for a plan (torch)."""
+    """Device output tensors for a plan (torch).  Short-fat plans: U column-major
+    M x k FP64 (stored k x M), V row-major N x k.  Tall plans: U row-major M x k
+    in the long-side type, V column-major N x k FP64 (stored k x N)."""
     import torch
     vdt = torch.float32 if plan.precision == "mixed" else torch.float64
+    if plan.tall:
+        U = torch.empty(plan.M, plan.k, dtype=vdt, device=device)
+        V = torch.empty(plan.k, plan.N, dtype=torch.float64, device=device)
+    else:
+        U = torch.empty(plan.k, plan.M, dtype=torch.float64, device=device)
+        V = torch.empty(plan.N, plan.k, dtype=vdt, device=device)
     out = {
         "sigma": torch.empty(plan.k, dtype=torch.float64, device=device),
-        "U": torch.empty(plan.k, plan.M, dtype=torch.float64, device=device),  # column-major M x k
-        "V": torch.empty(plan.N, plan.k, dtype=vdt, device=device),
+        "U": U,
+        "V": V,
         "rank": torch.zeros(1, dtype=torch.int32, device=device),
     }
     if with_patches:
-        out["patches"] = torch.zeros(plan.D * plan.M, 2, dtype=torch.int64, device=device)
+        out["patches"] = torch.zeros(plan.D * plan.Ms, 2, dtype=torch.int64, device=device)
         out["npatches"] = torch.zeros(1, dtype=torch.int64, device=device)
     return out
 
@@ -276,15 +288,15 @@ def svd(col_ptr, row_idx, vals, M, N, num_blocks, *, stream=None, plan: Plan | N
              out["patches"], out["npatches"], stream=stream)
     plan.sync()
     n = int(out["npatches"].item())
-    pr = out["patches"].view(-1)[: 2 * plan.D * plan.M].view(-1, 2)[:n]
+    pr = out["patches"].view(-1)[: 2 * plan.D * plan.Ms].view(-1, 2)[:n]
     # svd_patch = {int32 row, int32 block, int64 col}: decode the two int64 words
     row = (pr[:, 0] & 0xFFFFFFFF).to(torch.int64)
     blk = (pr[:, 0] >> 32).to(torch.int64)
     col = pr[:, 1]
     res = {
         "sigma": out["sigma"],
-        "U": out["U"].t(),
-        "V": out["V"],
+        "U": out["U"] if plan.tall else out["U"].t(),
+        "V": out["V"].t() if plan.tall else out["V"],
         "rank": int(out["rank"].item()),
         "patches": torch.stack([row, col], dim=1),
         "patch_blocks": blk,

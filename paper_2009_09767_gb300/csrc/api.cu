@@ -35,6 +35,7 @@ struct svd_plan_s {
     bool mixed = false, random = false;
     bool neighbor = false;  // Algorithm 3 (or 4 with the RandomChecker fallback)
     bool patched = false;   // any insertion mode
+    bool tall = false;      // SVD_FLAG_TALL: the caller's CSC is this problem's transpose
     double jac_tol = 0.0;
     int max_sweeps = 40, refine_iters = 1, merge_refine_iters = 3;
     std::vector<int64_t> bounds_h;
@@ -60,6 +61,18 @@ struct svd_plan_s {
     unsigned long long* cooc = nullptr; // neighbour modes: M x M row co-occurrence counts
     PatchRec* slots = nullptr;          // neighbour modes: one per lonely node
     int64_t* slot_ofs = nullptr;
+    // tall plans: the caller's CSC (of the N x M transpose of this problem) for
+    // the next run, and its transpose (this problem's CSC) with the scratch
+    const int64_t* src_col_ptr = nullptr;
+    const int32_t* src_row_idx = nullptr;
+    const void* src_vals = nullptr;
+    int64_t* t_ptr = nullptr;
+    int32_t* t_idx = nullptr;
+    char* t_val = nullptr;
+    int32_t* t_cnt = nullptr;
+    int64_t* t_tile = nullptr;
+    int32_t* t_tmp_idx = nullptr;
+    char* t_tmp_val = nullptr;
     double* G64 = nullptr;
     double* Gw64 = nullptr;    // FP64: Jacobi working copy
     double* Vt64 = nullptr;    // FP64 eigenvector rows (FP64 solve, or converted FP32 + refined)
@@ -138,8 +151,27 @@ struct Carver {
     }
 };
 
+// The short-and-fat problem a descriptor poses: A itself, or, for
+// SVD_FLAG_TALL, A^T (its column blocks are the row blocks of A).
+svd_desc short_fat(const svd_desc& d) {
+    svd_desc t = d;
+    if (d.flags & SVD_FLAG_TALL) {
+        t.M = (int32_t)std::min<int64_t>(d.N, INT32_MAX);
+        t.N = d.M;
+    }
+    return t;
+}
+
+svd_status validate_short_fat(const svd_desc* d);
+
 svd_status validate_desc(const svd_desc* d) {
     if (!d) return SVD_ERR_INVALID_ARG;
+    if ((d->flags & SVD_FLAG_TALL) && (d->M < 1 || d->N < 1)) return SVD_ERR_INVALID_ARG;
+    const svd_desc t = short_fat(*d);
+    return validate_short_fat(&t);
+}
+
+svd_status validate_short_fat(const svd_desc* d) {
     if (d->M < 1 || d->N < 1 || d->nnz < 0) return SVD_ERR_INVALID_ARG;
     if (d->value_type != SVD_VALUE_F32 && d->value_type != SVD_VALUE_F64) return SVD_ERR_INVALID_ARG;
     if (d->num_blocks < 1 || (int64_t)d->num_blocks > d->N) return SVD_ERR_INVALID_ARG;
@@ -172,6 +204,17 @@ void carve(svd_plan_s* p, Carver& c) {
     p->lonely = c.take<uint32_t>((size_t)D * p->W);
     p->patches = c.take<PatchRec>((size_t)D * M);
     p->patch_ofs = c.take<int64_t>(D + 1);
+    if (p->tall) {
+        const size_t sv = p->d.value_type == SVD_VALUE_F32 ? 4 : 8;
+        const int64_t nz = std::max<int64_t>(p->nnz, 1);
+        p->t_ptr = c.take<int64_t>(p->N + 1);
+        p->t_idx = c.take<int32_t>(nz);
+        p->t_val = c.take<char>(nz * sv);
+        p->t_cnt = c.take<int32_t>(p->N);
+        p->t_tile = c.take<int64_t>(transpose_scratch_words(p->N));
+        p->t_tmp_idx = c.take<int32_t>(nz);
+        p->t_tmp_val = c.take<char>(nz * sv);
+    }
     if (p->neighbor) {
         p->lonely_any = c.take<uint32_t>(p->W);
         p->cooc = c.take<unsigned long long>((size_t)M * M);
@@ -245,6 +288,7 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
     p->random = d->rank_fix == SVD_RANKFIX_RANDOM;
     p->neighbor = d->rank_fix == SVD_RANKFIX_NEIGHBOR || d->rank_fix == SVD_RANKFIX_NEIGHBOR_RANDOM;
     p->patched = p->random || p->neighbor;
+    p->tall = (d->flags & SVD_FLAG_TALL) != 0;
     p->use_oz = p->mixed && !(d->flags & SVD_FLAG_FP64_PRODUCTS);
     p->Mp = jacobi_pad(d->M);
     p->W = (d->M + 31) / 32;
@@ -347,6 +391,10 @@ svd_status phase_pre(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
     p->launches = 0;
     timing_begin(p, s);
     mark(p, 0, s);
+    if (p->tall)  // the caller's CSC is of the N x M transpose: form this problem's CSC
+        LAUNCH(p, 6, launch_transpose_csc(p->src_col_ptr, p->src_row_idx, p->src_vals, vt, p->N,
+                                          M, p->nnz, p->t_cnt, p->t_tile, p->t_tmp_idx,
+                                          p->t_tmp_val, p->t_ptr, p->t_idx, p->t_val, s));
     CU(cudaMemsetAsync(p->occ, 0, sizeof(uint32_t) * (size_t)D * p->W, s));
     CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
     LAUNCH(p, 1, launch_occupancy(io.col_ptr, io.row_idx, io.vals, vt, M, p->nchunks,
@@ -567,7 +615,8 @@ svd_status svd_plan_bytes(const svd_desc* desc, size_t* bytes) {
     svd_status st = validate_desc(desc);
     if (st != SVD_OK) return st;
     svd_plan_s tmp;
-    st = fill_plan(desc, &tmp);
+    const svd_desc sf = short_fat(*desc);
+    st = fill_plan(&sf, &tmp);
     if (st != SVD_OK) return st;
     Carver c{nullptr, 0, true};
     carve(&tmp, c);
@@ -585,7 +634,8 @@ svd_status plan_create(const svd_desc* desc, void* arena, size_t arena_bytes, sv
     if (st != SVD_OK) return st;
     svd_plan_s* p = new (std::nothrow) svd_plan_s();
     if (!p) return SVD_ERR_OOM;
-    st = fill_plan(desc, p);
+    const svd_desc sf = short_fat(*desc);
+    st = fill_plan(&sf, p);
     if (st != SVD_OK) { delete p; return st; }
     Carver dry{nullptr, 0, true};
     carve(p, dry);
@@ -654,16 +704,31 @@ svd_status svd_run(svd_plan_t p, const int64_t* d_col_ptr, const int32_t* d_row_
                    const void* d_vals, double* d_sigma, double* d_U, void* d_V, int32_t* d_rank,
                    svd_patch* d_patches, int64_t* d_npatches, void* stream) {
     if (!p || !d_col_ptr || (!d_row_idx && p->nnz > 0) || (!d_vals && p->nnz > 0) || !d_sigma ||
-        !d_U || !d_rank)
+        !d_rank)
         return SVD_ERR_INVALID_ARG;
-    if (!d_V && !(p->d.flags & SVD_FLAG_SKIP_V)) return SVD_ERR_INVALID_ARG;
+    // short-side (FP64, column-major) and long-side outputs; a tall plan's
+    // caller holds them as V and U
+    double* small = p->tall ? static_cast<double*>(d_V) : d_U;
+    void* big = p->tall ? static_cast<void*>(d_U) : d_V;
+    if (!small) return SVD_ERR_INVALID_ARG;
+    if (!big && !(p->d.flags & SVD_FLAG_SKIP_V)) return SVD_ERR_INVALID_ARG;
     if ((d_patches == nullptr) != (d_npatches == nullptr)) return SVD_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->d.flags & SVD_FLAG_CHECK_CSC) {
-        svd_status st = svd_check_csc(p->M, p->N, p->nnz, d_col_ptr, d_row_idx, stream);
+        // the caller's CSC: p->M x p->N, or N' = p->M columns of p->N rows when tall
+        const svd_status st =
+            p->tall ? svd_check_csc((int32_t)p->N, p->M, p->nnz, d_col_ptr, d_row_idx, stream)
+                    : svd_check_csc(p->M, p->N, p->nnz, d_col_ptr, d_row_idx, stream);
         if (st != SVD_OK) return st;
     }
-    return run_device(p, d_col_ptr, d_row_idx, d_vals, d_sigma, d_U, d_V, d_rank, d_patches,
+    if (p->tall) {
+        p->src_col_ptr = d_col_ptr;
+        p->src_row_idx = d_row_idx;
+        p->src_vals = d_vals;
+        return run_device(p, p->t_ptr, p->t_idx, p->t_val, d_sigma, small, big, d_rank,
+                          d_patches, d_npatches, s);
+    }
+    return run_device(p, d_col_ptr, d_row_idx, d_vals, d_sigma, small, big, d_rank, d_patches,
                       d_npatches, s);
 }
 
@@ -672,12 +737,17 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
                         int32_t* h_rank, svd_patch* h_patches, int64_t* h_npatches,
                         void* stream) {
     if (!p || !h_col_ptr || (!h_row_idx && p->nnz > 0) || (!h_vals && p->nnz > 0) || !h_sigma ||
-        !h_U || !h_rank)
+        !h_rank)
         return SVD_ERR_INVALID_ARG;
+    // short-side (FP64) and long-side outputs; a tall plan's caller holds them as V and U
+    double* h_small = p->tall ? static_cast<double*>(h_V) : h_U;
+    void* h_big = p->tall ? static_cast<void*>(h_U) : h_V;
+    if (!h_small) return SVD_ERR_INVALID_ARG;
+    const int64_t ncp = (p->tall ? p->M : p->N) + 1;  // column pointers of the caller's CSC
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t sv = p->d.value_type == SVD_VALUE_F32 ? 4 : 8;
     const size_t sV = p->mixed ? 4 : 8;
-    const bool want_v = h_V && !(p->d.flags & SVD_FLAG_SKIP_V);
+    const bool want_v = h_big && !(p->d.flags & SVD_FLAG_SKIP_V);
     // A page-locked V buffer is addressable from the device (unified
     // addressing; on this part over the chip-to-chip link): the SpMM then
     // streams V straight into it and the 2 GB copy disappears.  Not with
@@ -685,14 +755,14 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
     void* dV_direct = nullptr;
     if (want_v && !p->patched) {
         cudaPointerAttributes at{};
-        if (cudaPointerGetAttributes(&at, h_V) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        if (cudaPointerGetAttributes(&at, h_big) == cudaSuccess && at.type == cudaMemoryTypeHost &&
             at.devicePointer)
             dV_direct = at.devicePointer;
         cudaGetLastError();
     }
     const bool copy_v = want_v && !dV_direct;
     Carver dry{nullptr, 0, true};
-    dry.take<int64_t>(p->N + 1);
+    dry.take<int64_t>(ncp);
     dry.take<int32_t>(std::max<int64_t>(p->nnz, 1));
     dry.take<char>(std::max<int64_t>(p->nnz, 1) * sv);
     dry.take<double>(p->k);
@@ -712,7 +782,7 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
         p->host_arena_bytes = dry.off;
     }
     Carver c{p->host_arena, 0, false};
-    int64_t* cp = c.take<int64_t>(p->N + 1);
+    int64_t* cp = c.take<int64_t>(ncp);
     int32_t* ri = c.take<int32_t>(std::max<int64_t>(p->nnz, 1));
     char* va = c.take<char>(std::max<int64_t>(p->nnz, 1) * sv);
     double* sg = c.take<double>(p->k);
@@ -722,20 +792,23 @@ svd_status svd_run_host(svd_plan_t p, const int64_t* h_col_ptr, const int32_t* h
     int32_t* rk_ = c.take<int32_t>(1);
     svd_patch* pt = c.take<svd_patch>((size_t)p->D * p->M);
     int64_t* np = c.take<int64_t>(1);
-    CU(cudaMemcpyAsync(cp, h_col_ptr, sizeof(int64_t) * (p->N + 1), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(cp, h_col_ptr, sizeof(int64_t) * ncp, cudaMemcpyHostToDevice, s));
     if (p->nnz > 0) {
         CU(cudaMemcpyAsync(ri, h_row_idx, sizeof(int32_t) * p->nnz, cudaMemcpyHostToDevice, s));
         CU(cudaMemcpyAsync(va, h_vals, sv * p->nnz, cudaMemcpyHostToDevice, s));
     }
     const int saved = p->d.flags;
     if (!want_v) p->d.flags |= SVD_FLAG_SKIP_V;
-    svd_status st = svd_run(p, cp, ri, va, sg, U, want_v ? V : nullptr, rk_, pt, np, stream);
+    void* Vb = want_v ? static_cast<void*>(V) : nullptr;
+    svd_status st = p->tall ? svd_run(p, cp, ri, va, sg, static_cast<double*>(Vb), U, rk_, pt,
+                                      np, stream)
+                            : svd_run(p, cp, ri, va, sg, U, Vb, rk_, pt, np, stream);
     p->d.flags = saved;
     if (st != SVD_OK) return st;
     CU(cudaMemcpyAsync(h_sigma, sg, sizeof(double) * p->k, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(h_U, U, sizeof(double) * p->M * p->k, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h_small, U, sizeof(double) * p->M * p->k, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h_rank, rk_, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    if (copy_v) CU(cudaMemcpyAsync(h_V, V, (size_t)p->N * p->k * sV, cudaMemcpyDeviceToHost, s));
+    if (copy_v) CU(cudaMemcpyAsync(h_big, V, (size_t)p->N * p->k * sV, cudaMemcpyDeviceToHost, s));
     if (h_npatches) CU(cudaMemcpyAsync(h_npatches, np, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (h_patches)
         CU(cudaMemcpyAsync(h_patches, pt, sizeof(svd_patch) * (size_t)p->D * p->M,
@@ -1088,6 +1161,8 @@ svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, s
     *out = nullptr;
     for (int i = 0; i < n; ++i)
         if (!plans[i]) return SVD_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (plans[i]->tall) return SVD_ERR_UNSUPPORTED;
     size_t items = 0;
     for (int i = 0; i < n; ++i) items += (size_t)plans[i]->D + 1;
     svd_batch_t b = nullptr;

@@ -167,6 +167,18 @@ template <typename T>
 cudaError_t launch_spmm_patches(const PatchRec* patches, const int64_t* npatches_dev,
                                 int max_patches, int k, const T* W, T* V, cudaStream_t s);
 
+// ---- transpose.cu: CSC of A^T from the CSC of a tall A ---------------------------
+// A is rows x cols (cols <= 1024); writes t_ptr (rows + 1), t_idx and t_val
+// (nnz each, the CSC of A^T with sorted row indices).  Scratch: cnt (rows
+// int32), tile_sum (transpose_scratch_words(rows) int64), tmp_idx / tmp_val
+// (nnz each).  Six kernels and one memset.
+cudaError_t launch_transpose_csc(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
+                                 int value_type, int64_t rows, int cols, int64_t nnz,
+                                 int32_t* cnt, int64_t* tile_sum, int32_t* tmp_idx,
+                                 void* tmp_val, int64_t* t_ptr, int32_t* t_idx, void* t_val,
+                                 cudaStream_t s);
+size_t transpose_scratch_words(int64_t rows);
+
 // ---- misc ---------------------------------------------------------------------
 cudaError_t launch_check_csc(int M, int64_t N, int64_t nnz, const int64_t* col_ptr,
                              const int32_t* row_idx, int32_t* bad, cudaStream_t s);

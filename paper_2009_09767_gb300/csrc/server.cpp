@@ -450,6 +450,7 @@ svd_status svd_server_create(size_t budget_bytes, int32_t max_inflight, svd_serv
 svd_status svd_server_submit(svd_server_t s, const svd_request* req, uint64_t* ticket) {
     if (!s || !req || !ticket || !req->h_col_ptr || !req->h_sigma || !req->h_U || !req->h_rank)
         return SVD_ERR_INVALID_ARG;
+    if (req->desc.flags & SVD_FLAG_TALL) return SVD_ERR_UNSUPPORTED;
     size_t plan_bytes = 0;
     svd_status st = svd_plan_bytes(&req->desc, &plan_bytes);
     if (st != SVD_OK) return st;

@@ -31,6 +31,15 @@ Workloads (sizes as named by the workload, not by the paper, whose own
                          spread row, the odd ones in columns of their own), four
                          columns of 40 spread rows, 24 stored zeros (some beside
                          the lone rows), rows 93-95 empty.
+* ``paper_bipartite``    0/1 pattern of the paper's matrix shape (539 x 170897,
+                         the private job-candidate data); row m is Bernoulli(
+                         density * a_m) over the columns, a_m lognormal(0, 0.5)
+                         activities scaled to mean 1.  The paper does not state
+                         its density, so tests sweep it.
+* ``tall_skinny``        the row-block case: M=20011 rows, N=96 columns,
+                         Bernoulli(0.012) pattern, N(0,1) values, 7 row blocks
+                         (M not divisible by 7), columns 0, 5, ..., 45 emptied
+                         inside the third row block (lonely nodes of A^T).
 * ``arrival_stream``     Poisson arrivals of batch_mix-shaped requests with 5%
                          zipf_wide-shaped ones.
 """
@@ -307,6 +316,45 @@ def neighbor_mix(seed: int = SEED_BASE + 6, dtype=np.float64) -> CscCase:
     vals = V[rows, cols].astype(dtype)
     return CscCase("neighbor_mix", M, N, col_ptr, rows.astype(np.int32), vals, D,
                    widths.astype(np.int64), k=M, seed=seed)
+
+
+def paper_bipartite(density: float, seed: int = SEED_BASE + 7, M: int = 539,
+                    N: int = 170_897, activity_sigma: float = 0.5) -> CscCase:
+    """0/1 bipartite pattern (values 1.0, float32) of the paper's matrix
+    shape; see the module docstring."""
+    rng = np.random.default_rng(seed)
+    a = np.exp(rng.normal(0.0, activity_sigma, size=M))
+    p = np.minimum(density * a / a.mean(), 1.0)
+    cols, rows = [], []
+    for m in range(M):
+        c = np.nonzero(rng.random(N) < p[m])[0]
+        cols.append(c)
+        rows.append(np.full(c.shape[0], m, dtype=np.int64))
+    cols = np.concatenate(cols)
+    rows = np.concatenate(rows)
+    order = np.lexsort((rows, cols))
+    cols, rows = cols[order], rows[order]
+    col_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(cols, minlength=N), out=col_ptr[1:])
+    vals = np.ones(rows.shape[0], dtype=np.float32)
+    return CscCase(f"paper_bipartite_{density:g}", M, N, col_ptr, rows.astype(np.int32), vals,
+                   1, None, k=M, seed=seed)
+
+
+def tall_skinny(seed: int = SEED_BASE + 8, M: int = 20011, N: int = 96, D: int = 7,
+                density: float = 0.012, dtype=np.float64) -> CscCase:
+    """Tall A (see the module docstring); num_blocks counts ROW blocks."""
+    rng = np.random.default_rng(seed)
+    col_ptr, row_idx = bernoulli_csc(rng, M, N, density)
+    vals = rng.standard_normal(row_idx.shape[0]).astype(dtype)
+    cols = np.repeat(np.arange(N, dtype=np.int64), np.diff(col_ptr))
+    lo, hi = 2 * (M // D), 3 * (M // D)          # third row block of the equal split
+    drop = (cols % 5 == 0) & (cols < 50) & (row_idx >= lo) & (row_idx < hi)
+    keep = ~drop
+    col_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(cols[keep], minlength=N), out=col_ptr[1:])
+    return CscCase("tall_skinny", M, N, col_ptr, row_idx[keep], vals[keep], D, None, k=N,
+                   seed=seed)
 
 
 def random_dense_csc(rng: np.random.Generator, M: int, N: int, density: float,

@@ -103,6 +103,23 @@ def test_plan_bytes_validation(lib):
     assert _bytes(lib, **{**ok, "bounds": [0, 1, 2, 3, 4096]})[0] == 0
 
 
+def test_tall_plan_bytes_validation(lib):
+    """SVD_FLAG_TALL: M is the long side (any), N <= 1024, row blocks over M."""
+    tall = dict(M=100_000, N=96, nnz=5000, num_blocks=8, flags=rk.FLAG_TALL)
+    st, n = _bytes(lib, **tall)
+    assert st == 0 and n > 0
+    # the transpose buffers: the same problem stated short and fat needs less
+    st2, n2 = _bytes(lib, **{**tall, "M": 96, "N": 100_000, "flags": 0})
+    assert st2 == 0 and n > n2
+    assert _bytes(lib, **{**tall, "N": 1025})[0] == 8          # short side above 1024
+    assert _bytes(lib, **{**tall, "num_blocks": 100_001})[0] == 1
+    assert _bytes(lib, **{**tall, "k": 97})[0] == 1
+    assert _bytes(lib, **{**tall, "bounds": [0] + [12_500 * i for i in range(1, 8)] +
+                          [100_000]})[0] == 0
+    assert _bytes(lib, **{**tall, "bounds": [0] + [12_500 * i for i in range(1, 8)] +
+                          [96]})[0] == 1
+
+
 def test_null_plan_is_rejected(lib):
     assert lib.svd_sync(None) == 1
     assert lib.svd_query(None, 1, 0, None, 0) == 1

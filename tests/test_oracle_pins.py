@@ -292,6 +292,46 @@ def test_neighbor_sparse_equals_dense():
         assert S.tolist() == P.tolist()
 
 
+def test_svd_tall_against_lapack_and_reconstruction():
+    """The tall form returns factors of A' itself: A' = U diag(s) V^T with
+    orthonormal U (M x N) and V, and s equal to LAPACK's singular values; an
+    insertion given as (column of A, row of A) lands at A'[row, column]."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((300, 7)) * (rng.random((300, 7)) < 0.2)
+    col_ptr, row_idx, vals = _csc(A)
+    pt = np.asarray([[2, 5], [6, 299]], dtype=np.int64)
+    s, U, V, sweeps = oracle.svd_tall(col_ptr, row_idx, vals, 300, 7, pt)
+    assert sweeps > 0
+    Ap = A.copy()
+    Ap[5, 2] += 1.0
+    Ap[299, 6] += 1.0
+    assert U.shape == (300, 7) and V.shape == (7, 7)
+    assert np.abs(U @ np.diag(s) @ V.T - Ap).max() <= 1e-12 * np.abs(Ap).max()
+    assert np.abs(U.T @ U - np.eye(7)).max() <= 1e-12
+    assert np.abs(s - np.linalg.svd(Ap, compute_uv=False)).max() <= 1e-12 * s[0]
+
+
+def test_svd_gram_01_against_jacobi_and_closed_form():
+    """The exact-cross-product SVD of a 0/1 matrix agrees with the Jacobi SVD
+    (both with insertions), and reproduces a closed form: k disjoint rows of
+    lengths n_1..n_k have singular values sqrt(n_i)."""
+    rng = np.random.default_rng(8)
+    A = (rng.random((12, 300)) < 0.05).astype(np.float64)
+    col_ptr, row_idx, vals = _csc(A)
+    patches = np.asarray([[3, 17], [5, 250]], dtype=np.int64)
+    s, U = oracle.svd_gram_01(col_ptr, row_idx, vals, 12, 300, patches)
+    sj, Uj, _, _ = oracle.svd_csc(col_ptr, row_idx, vals, 12, 300, patches)
+    assert np.abs(s - sj).max() <= 1e-12 * sj[0]
+    assert np.abs(np.abs(U.T @ Uj) - np.eye(12)).max() <= 1e-9
+    B = np.zeros((3, 20))
+    B[0, 0:4] = 1; B[1, 4:13] = 1; B[2, 13:14] = 1
+    s2, U2 = oracle.svd_gram_01(*_csc(B), 3, 20)
+    assert np.allclose(s2, [3.0, 2.0, 1.0], rtol=0, atol=1e-14)
+    assert np.allclose(np.abs(U2), np.eye(3)[[1, 0, 2]].T, atol=1e-14)
+    with pytest.raises(ValueError):
+        oracle.svd_gram_01(*_csc(B * 0.5), 3, 20)
+
+
 # --------------------------------------------------------------------------
 # Eq. 2 block cross product and the proxy identity of Eqs. 2-3
 
