@@ -292,6 +292,22 @@ def test_neighbor_sparse_equals_dense():
         assert S.tolist() == P.tolist()
 
 
+def test_neighbor_sparse_equals_dense_on_neighbor_mix():
+    """The closed-form evaluator agrees with the literal lists on the GPU
+    parity case (long columns, stored zeros, empty lists), both modes."""
+    c = synth.neighbor_mix()
+    b = np.concatenate([[0], np.cumsum(c.widths)]).astype(np.int64)
+    A = oracle.densify(c.col_ptr, c.row_idx, c.vals, c.M, c.N)
+    lon, rne = oracle.lonely_dense(A, b)
+    fix = lon & rne[None, :]
+    for fb in (False, True):
+        P = oracle.neighbor_patches(A, b, fix, 77, fallback_random=fb)
+        S = oracle.neighbor_patches_sparse(c.col_ptr, c.row_idx, c.vals, c.M, b, fix, 77,
+                                           fallback_random=fb)
+        assert S.tolist() == P.tolist()
+    assert 0 < len(oracle.neighbor_patches(A, b, fix, 77)) < int(fix.sum())
+
+
 def test_svd_tall_against_lapack_and_reconstruction():
     """The tall form returns factors of A' itself: A' = U diag(s) V^T with
     orthonormal U (M x N) and V, and s equal to LAPACK's singular values; an
