@@ -35,10 +35,30 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SVDs/sec & HBM GB/s at σ rel err ≤1e-4; serving p50/p99 latency vs plain FP64"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
+
+
+def fp32_peak(device) -> dict:
+    """FP32 FMA peak from the device's own SM count and the maximum SM clock
+    (MEASURED_PEAKS.json, else nvidia-smi's clocks.max.sm)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz, src = None, None
+    peaks = measured_peaks()
+    if peaks and peaks.get("sm_max_mhz"):
+        mhz, src = float(peaks["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    if mhz is None:
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={device.index or 0}",
+                                  "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=10).stdout
+            mhz, src = float(out.strip().splitlines()[0]), "nvidia-smi clocks.max.sm"
+        except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+            mhz, src = 2070.0, "nominal 2070 MHz"
+    tf = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return {"tflops": tf, "sms": sms, "mhz": mhz,
+            "source": f"{sms} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                      f"{mhz:g} MHz ({src})"}
 
 
 def dist_env():
@@ -121,11 +141,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM traffic of one block-Jacobi launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) on a 16-matrix launch (zipf_wide with 250k columns), per matrix,
-# with the hash of the kernel source it was taken on; reported as null once the source
-# changes.  See profiles/k_jacobi4_zipf_wide_250k.md.
-JACOBI_TRAFFIC = {"source_sha256_16": "d2d23d852db35f79", "bytes_per_matrix": (17236736 + 2764032) / 16}
+# DRAM traffic of one block-Jacobi launch, as a stored note: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of a 16-matrix launch (zipf_wide with 250k
+# columns), per matrix, with the hash of the kernel source it was taken on.  The line
+# reports it (scaled to the launch, labelled as stored) only while the source is unchanged.
+JACOBI_TRAFFIC = {"source_sha256_16": "none", "bytes_per_matrix": None}
 
 
 def source_hash(rel: str) -> str:
@@ -145,6 +165,27 @@ def jacobi_flops(sweeps: np.ndarray, Mp: int) -> float:
     per_step = (n_p * (n_p + 1) / 2 * 2 * 2 * 32 ** 3 + n_p * (Mp // 32) * 2 * 32 ** 3
                 + n_p * 31 * 16 * 6 * 3 * 32)
     return float(np.sum(np.abs(sweeps))) * steps * per_step
+
+
+def accuracy_vs(s, U, s_ref, U_ref, gap=1e-3):
+    """Largest relative sigma error (sigma > 1e-10 sigma_1) and the largest
+    principal-angle sine over the singular vectors whose sigma is separated
+    from both neighbours by gap * sigma_1 (U columns = vectors)."""
+    s1 = float(s_ref[0])
+    big = s_ref > 1e-10 * s1
+    rel = float(np.max(np.abs(s[big] - s_ref[big]) / s_ref[big])) if big.any() else 0.0
+    worst = 0.0
+    n = len(s_ref)
+    for i in range(n):
+        if not big[i]:
+            continue
+        if (i > 0 and s_ref[i - 1] - s_ref[i] < gap * s1) or (i + 1 < n and s_ref[i] - s_ref[i + 1] < gap * s1):
+            continue
+        a = U[:, i] / max(np.linalg.norm(U[:, i]), 1e-300)
+        b = U_ref[:, i] / max(np.linalg.norm(U_ref[:, i]), 1e-300)
+        worst = max(worst, float(np.linalg.norm(a - (a @ b) * b)))
+    return {"sigma_max_rel_err": rel, "u_max_angle_sine_separated": worst,
+            "tolerance": {"sigma_rel": 1e-4, "angle": 1e-4}}
 
 
 def algorithmic_bytes(case, R: int, k: int, s_v: int) -> float:
@@ -305,27 +346,23 @@ def run_batch(args):
         p.free()
 
 
-def run_serve(args):
+def serve_sweep(prec_rates, duration, grace, max_inflight=16, seed_offset=0):
     """Serving: Poisson arrivals of batch_mix-shaped requests with 5%
     zipf_wide-shaped ones, 40 GB device budget; p50/p99 latency (arrival to
-    results on the host) and completed requests/s, per arrival rate."""
+    results on the host) and completed requests/s, per (precision, rate).
+    prec_rates: [(precision, rate), ...].  Requests still queued `grace`
+    seconds after the last arrival are cancelled and counted as dropped."""
     import torch
 
     import paper_2009_09767_gb300 as rk
     import synth
 
     torch.cuda.set_device(0)
-    rng = np.random.default_rng(synth.SEED_BASE + 5)
+    rng = np.random.default_rng(synth.SEED_BASE + 5 + seed_offset)
     templates = synth.batch_mix(256, seed=synth.SEED_BASE + 5)
     for c in templates:
         c.num_blocks = 1
     wide = synth.zipf_wide()
-    out = {"metric": "serving p50/p99 latency and throughput", "unit": "ms", "data": "synthetic",
-           "config": {"workload": "Poisson arrivals, 95% batch_mix-shaped, 5% zipf_wide-shaped "
-                                  "(512 x 1e6), V copied back", "budget_bytes": 40 << 30,
-                      "max_inflight": 16, "duration_s_per_rate": args.duration,
-                      "grace_s": args.grace},
-           "rates": []}
     pinned = {}
 
     def outputs_for(c, prec, slot):
@@ -334,68 +371,82 @@ def run_serve(args):
             pinned[key] = rk.host_outputs(c.M, c.N, min(c.M, c.N), prec, pinned=True)
         return pinned[key]
 
-    for prec in ("mixed", "fp64"):
-        for rate in [float(r) for r in args.rates.split(",")]:
-            srv = rk.Server(40 << 30, max_inflight=16)
-            n = max(1, int(rate * args.duration))
-            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
-            kinds = rng.random(n) < 0.05
-            picks = rng.integers(0, len(templates), size=n)
-            tickets = []
-            t_start = time.perf_counter()
-            wide_slot = 0
-            for i in range(n):
-                delay = t_start + arrivals[i] - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-                if kinds[i]:
-                    c, slot = wide, wide_slot % 3
-                    wide_slot += 1
-                else:
-                    c, slot = templates[picks[i]], i % 4
-                o = outputs_for(c, prec, slot)
-                tickets.append(srv.submit(c.M, c.N, c.col_ptr, c.row_idx, c.vals, c.num_blocks, o,
-                                          precision=prec))
-            # requests still queued a grace period after the last arrival are
-            # cancelled, all at once, and counted as dropped (an overloaded
-            # server would otherwise drain its backlog for minutes); admitted
-            # ones finish
-            deadline = t_start + args.duration + args.grace
-            status = {}
-            for t in tickets:
-                call, st = srv.wait_status(t, max(0.0, deadline - time.perf_counter()))
-                if call == 0:
-                    status[t] = st
-            dropped = 0
-            for t in tickets:
-                if t not in status and srv.cancel(t) == 0:
-                    srv.wait_status(t, 60.0)
-                    status[t] = None
-                    dropped += 1
-            lat, fails, last_done = [], 0, 0.0
-            first = None
-            for t in tickets:
-                if t in status and status[t] is None:
-                    srv.release(t)
-                    continue
-                st = status[t] if t in status else srv.wait(t, timeout=120.0)
-                ts, ta, td = srv.times(t)
-                first = ts if first is None else min(first, ts)
-                last_done = max(last_done, td)
-                if st != 0:
-                    fails += 1
-                else:
-                    lat.append((td - ts) * 1e3)
+    results = []
+    for prec, rate in prec_rates:
+        srv = rk.Server(40 << 30, max_inflight=max_inflight)
+        n = max(1, int(rate * duration))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        kinds = rng.random(n) < 0.05
+        picks = rng.integers(0, len(templates), size=n)
+        tickets = []
+        t_start = time.perf_counter()
+        wide_slot = 0
+        for i in range(n):
+            delay = t_start + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if kinds[i]:
+                c, slot = wide, wide_slot % 3
+                wide_slot += 1
+            else:
+                c, slot = templates[picks[i]], i % 4
+            o = outputs_for(c, prec, slot)
+            tickets.append(srv.submit(c.M, c.N, c.col_ptr, c.row_idx, c.vals, c.num_blocks, o,
+                                      precision=prec))
+        # requests still queued a grace period after the last arrival are
+        # cancelled, all at once, and counted as dropped (an overloaded
+        # server would otherwise drain its backlog for minutes); admitted
+        # ones finish
+        deadline = t_start + duration + grace
+        status = {}
+        for t in tickets:
+            call, st = srv.wait_status(t, max(0.0, deadline - time.perf_counter()))
+            if call == 0:
+                status[t] = st
+        dropped = 0
+        for t in tickets:
+            if t not in status and srv.cancel(t) == 0:
+                srv.wait_status(t, 60.0)
+                status[t] = None
+                dropped += 1
+        lat, fails, last_done = [], 0, 0.0
+        first = None
+        for t in tickets:
+            if t in status and status[t] is None:
                 srv.release(t)
-            stats = srv.stats()
-            srv.close()
-            out["rates"].append({
-                "precision": prec, "rate_req_s": rate, "requests": n, "failed": fails,
-                "dropped_after_grace": dropped,
-                "completed_per_s": len(lat) / max(last_done - first, 1e-9),
-                "p50_ms": float(np.percentile(lat, 50)) if lat else None,
-                "p99_ms": float(np.percentile(lat, 99)) if lat else None,
-                "pool_peak_gb": stats["pool_peak"] / 2**30})
+                continue
+            st = status[t] if t in status else srv.wait(t, timeout=120.0)
+            ts, ta, td = srv.times(t)
+            first = ts if first is None else min(first, ts)
+            last_done = max(last_done, td)
+            if st != 0:
+                fails += 1
+            else:
+                lat.append((td - ts) * 1e3)
+            srv.release(t)
+        stats = srv.stats()
+        srv.close()
+        results.append({
+            "precision": prec, "rate_req_s": rate, "requests": n, "failed": fails,
+            "dropped_after_grace": dropped,
+            "completed_per_s": len(lat) / max(last_done - first, 1e-9) if first is not None else 0.0,
+            "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+            "pool_peak_gb": stats["pool_peak"] / 2**30})
+    return results
+
+
+def run_serve(args):
+    """Serving sweep over args.rates for both precisions (one JSON line)."""
+    rates = [float(r) for r in args.rates.split(",")]
+    res = serve_sweep([(p, r) for p in ("mixed", "fp64") for r in rates], args.duration,
+                      args.grace)
+    out = {"metric": "serving p50/p99 latency and throughput", "unit": "ms", "data": "synthetic",
+           "config": {"workload": "Poisson arrivals, 95% batch_mix-shaped, 5% zipf_wide-shaped "
+                                  "(512 x 1e6), V copied back", "budget_bytes": 40 << 30,
+                      "max_inflight": 16, "duration_s_per_rate": args.duration,
+                      "grace_s": args.grace},
+           "rates": res}
     print(json.dumps(out), flush=True)
 
 
@@ -496,6 +547,14 @@ def main():
                     choices=["truncate", "random", "neighbor", "neighbor_random"],
                     help="large/small: rank fix (Algorithms 2-4); the headline is truncate")
     ap.add_argument("--seed", type=int, default=1, help="rank-fix key")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="zipf_wide: skip the plain FP64 arm (same matrix, --precision fp64)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="zipf_wide: skip the bounded serving sweep")
+    ap.add_argument("--serve-rates", default="mixed:100,mixed:500,fp64:100",
+                    help="zipf_wide: serving sweep as precision:rate pairs")
+    ap.add_argument("--serve-duration", type=float, default=3.0)
+    ap.add_argument("--serve-grace", type=float, default=3.0)
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -599,17 +658,17 @@ def main():
     jac_flops = jacobi_flops(sweeps[:-1], Mp)
     achieved = jac_flops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else 0.0
     jac_kernel = "k_jacobi4" if args.precision == "mixed" else "k_jacobi<double>"
+    fpk = fp32_peak(dev)
     roofline = {"kernel": f"{jac_kernel} ({case.num_blocks} blocks of 512 x 512)",
                 "bound": "alu",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts "
-                               "and maximum clock)",
+                "achieved": achieved, "peak": fpk["tflops"], "unit": "TFLOP/s",
+                "frac": achieved / fpk["tflops"], "peak_source": fpk["source"],
                 "traffic": None, "kernel_ms": jac_ms, "algorithmic_flops": jac_flops}
-    if source_hash("paper_2009_09767_gb300/csrc/jacobi.cu") == JACOBI_TRAFFIC["source_sha256_16"]:
+    if (JACOBI_TRAFFIC["bytes_per_matrix"] and source_hash("paper_2009_09767_gb300/csrc/jacobi.cu")
+            == JACOBI_TRAFFIC["source_sha256_16"]):
         roofline["traffic"] = JACOBI_TRAFFIC["bytes_per_matrix"] * case.num_blocks
-        roofline["traffic_note"] = ("ncu dram bytes of a 16-matrix launch, scaled by matrices "
-                                    "to this launch")
+        roofline["traffic_note"] = ("stored: ncu dram bytes of one 16-matrix launch of this "
+                                    "source, scaled by matrices to this launch")
     bytes_per_svd = algorithmic_bytes(case, R, plan.k, s_v)
     peaks = measured_peaks()
     hbm = {"algorithmic_bytes_per_svd": bytes_per_svd,
@@ -631,6 +690,50 @@ def main():
         gbs = nbytes / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0
         hbm_kernels[name] = {"algorithmic_bytes": float(nbytes), "ms": ms_k, "gbs": gbs,
                              "frac": gbs / hbm["peak_gbs"]}
+
+    # the plain FP64 GPU method on the same matrix (the comparison the metric
+    # names) and the mixed result's accuracy against it
+    plain = None
+    if rank == 0 and ws == 1 and not args.no_plain and args.precision == "mixed":
+        s_mixed = out["sigma"].cpu().numpy()
+        U_mixed = out["U"].cpu().numpy().T
+        pp = rk.Plan(case.M, case.N, case.nnz, case.num_blocks, value_type=vt, precision="fp64")
+        po = rk.alloc_outputs(pp, device=dev, with_patches=False)
+        pp.run(cp, ri, va, po["sigma"], po["U"], po["V"], po["rank"], stream=stream)
+        pp.sync()
+        n_plain = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n_plain):
+            pp.run(cp, ri, va, po["sigma"], po["U"], po["V"], po["rank"], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pp.sync()
+        plain_ms = e0.elapsed_time(e1) / n_plain
+        s64 = po["sigma"].cpu().numpy()
+        U64 = po["U"].cpu().numpy().T
+        pp.free()
+        acc = accuracy_vs(s_mixed, U_mixed, s64, U64)
+        plain = {"value": 1e3 / plain_ms, "unit": "SVD/s", "ms_per_step": plain_ms,
+                 "steps": n_plain, "precision": "fp64",
+                 "method": "the same library with precision=FP64, one svd_run per step, "
+                           "inputs resident on the device",
+                 "mixed_over_plain": value / (1e3 / plain_ms),
+                 "mixed_accuracy_vs_plain": acc}
+
+    serving = None
+    if rank == 0 and ws == 1 and not args.no_serve:
+        pr = []
+        for item in args.serve_rates.split(","):
+            prec, rate = item.split(":")
+            pr.append((prec, float(rate)))
+        t_srv = time.perf_counter()
+        serving = {"workload": "Poisson arrivals, 95% batch_mix-shaped, 5% zipf_wide-shaped; "
+                               "40 GB budget; results copied to pinned host memory",
+                   "duration_s_per_rate": args.serve_duration, "grace_s": args.serve_grace,
+                   "rates": serve_sweep(pr, args.serve_duration, args.serve_grace)}
+        serving["wall_s"] = time.perf_counter() - t_srv
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -659,6 +762,7 @@ def main():
                        "l2": "no flush: each step writes V (N x k, >= 2 GB) and a >= 0.5 GB "
                              "workspace, far above the 129 MB L2"},
             "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "plain_fp64": plain, "serving": serving,
             "gpu_launches": launches * args.steps, "launches_per_step": launches,
             "clocks": clock_info, "stage_ms": stage_ms, "hbm_kernels": hbm_kernels,
             "sweeps": {"blocks_min": int(np.abs(sweeps[:-1]).min()),

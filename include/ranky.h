@@ -109,6 +109,25 @@ typedef struct {
     int32_t refine_iters;            /* mixed mode: FP64 refinement steps of each
                                         block eigenbasis, < 0 = default (1) */
     int32_t flags;                   /* SVD_FLAG_* */
+    int32_t merge_arity;             /* proxy merge: 0 or 1 = one level (section III,
+                                        Fig. 1: the SVD of P = [U^1 S^1 | ... |
+                                        U^D S^D]); a >= 2 = a tree in which every
+                                        node merges a consecutive children (the
+                                        multi-level merge of Iwen and Ong that
+                                        section II describes and section III
+                                        specialises): node matrix S = sum of the
+                                        children's Y^T Y, Y = their S U^T, then its
+                                        eigendecomposition, level by level up to
+                                        the root.  P is never formed: the plan
+                                        needs M * R * 8 bytes (R = sum of block
+                                        ranks <= D M) less device memory.
+                                        Rejected by svd_batch_create and run alone
+                                        by the server. */
+    int32_t merge_rank;              /* k' > 0: every block (and tree node) passes at
+                                        most its k' largest singular directions
+                                        upward (the approximate truncation of the
+                                        multi-level merge; k' >= k required); 0 =
+                                        its numerical rank (exact) */
 } svd_desc;
 
 #define SVD_FLAG_CHECK_CSC 1   /* svd_run validates the CSC first (synchronous) */
@@ -122,6 +141,10 @@ typedef struct {
                                  P P^T with FP64 arithmetic instead of exact 8-bit
                                  slices on the bf16 tensor cores (for testing and
                                  timing) */
+#define SVD_FLAG_LEGACY_MMA 64 /* mixed precision: run the exact-slice products on the
+                                 warp-level mma.sync tensor path instead of tcgen05.mma
+                                 with TMEM accumulators (bit-identical results; for
+                                 testing and timing) */
 #define SVD_FLAG_TALL 32       /* tall-and-skinny A: M rows (any, >= 1) and N <= 1024
                                  columns, split into num_blocks ROW blocks (the row-block
                                  form of section II); block_col_bounds then holds D+1
@@ -334,6 +357,37 @@ svd_status svd_right_vectors_static(int32_t M, int64_t N, int64_t nnz, int32_t v
                                     const svd_patch* d_patches, const int64_t* d_npatches,
                                     int64_t max_patches, int32_t v_type, void* d_V,
                                     void* stream);
+
+/* ---- FP64-accurate dense product on the tensor cores -----------------------
+ * C = A B^T for FP64 A (m x k, row-major, leading dimension lda) and B
+ * (n x k, ldb), the product behind the merge's P P^T (section III, Eq. 3:
+ * P P^* = A A^*) and the mixed-precision refinement of every block basis.
+ * Each row is scaled by its power-of-two magnitude bound and cut into
+ * `slices` (3 or 5) signed 8-bit integer slices (exact in bf16); every pair of
+ * slices whose weights are within the kept range is multiplied on the bf16
+ * tensor cores with exact integer sums, and the sums are combined in 64-bit
+ * integers and converted to FP64 once (error-free splitting after Ozaki et
+ * al., Numer. Algorithms 59, 2012).  The error is below about
+ * 2^(2 - 8 slices) k 2^(e_i + e_j), e_i the exponent bound of row i of A, e_j
+ * of row j of B (5 slices: ~2^-38 k of the row scales).
+ *   m, n          1 .. 2^20; k >= 1
+ *   d_C           row-major m x n (ldc >= n), overwritten
+ *   flags         SVD_PRODUCT_SYM: B is A (n == m, d_B ignored); only the
+ *                 upper triangle is formed, then mirrored.
+ *                 SVD_PRODUCT_LEGACY_MMA: warp-level mma.sync instead of
+ *                 tcgen05.mma with TMEM accumulators (bit-identical result)
+ *   d_work        device scratch of svd_exact_product_bytes(...) bytes,
+ *                 caller-owned; nothing is allocated
+ *   d_err         device int32 (may be NULL), set to 1 when a bounded wait of
+ *                 the tcgen05 kernel ran out (its tile is then not written)
+ * Asynchronous on `stream`; argument errors return synchronously. */
+#define SVD_PRODUCT_SYM 1
+#define SVD_PRODUCT_LEGACY_MMA 2
+size_t svd_exact_product_bytes(int32_t m, int32_t n, int64_t k, int32_t slices);
+svd_status svd_exact_product(int32_t m, int32_t n, int64_t k, const double* d_A, int64_t lda,
+                             const double* d_B, int64_t ldb, double* d_C, int64_t ldc,
+                             int32_t slices, int32_t flags, void* d_work, size_t work_bytes,
+                             int32_t* d_err, void* stream);
 
 void svd_free(svd_plan_t plan);
 const char* svd_status_str(svd_status s);

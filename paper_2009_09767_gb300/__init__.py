@@ -36,6 +36,7 @@ FLAG_TIMING = 4
 FLAG_DENSE_REFINE = 8
 FLAG_FP64_PRODUCTS = 16
 FLAG_TALL = 32
+FLAG_LEGACY_MMA = 64
 STAGES = ["partition", "gram", "block_jacobi", "block_refine", "sort_proxy", "merge_gram",
           "merge_eig", "finalize", "spmm"]
 
@@ -60,6 +61,7 @@ class SvdDesc(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("rank_tol", ctypes.c_double),
         ("max_sweeps", ctypes.c_int32), ("jacobi_tol", ctypes.c_double),
         ("refine_iters", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("merge_arity", ctypes.c_int32), ("merge_rank", ctypes.c_int32),
     ]
 
 
@@ -109,7 +111,7 @@ def _check(status: int, what: str):
 
 def make_desc(M, N, nnz, num_blocks, *, bounds=None, k=0, precision="mixed",
               rank_fix="truncate", seed=0, value_type="f32", rank_tol=0.0, max_sweeps=0,
-              jacobi_tol=0.0, refine_iters=-1, flags=0):
+              jacobi_tol=0.0, refine_iters=-1, flags=0, merge_arity=0, merge_rank=0):
     d = SvdDesc()
     d.M, d.N, d.nnz = int(M), int(N), int(nnz)
     d.value_type = VALUE[value_type] if isinstance(value_type, str) else int(value_type)
@@ -127,6 +129,8 @@ def make_desc(M, N, nnz, num_blocks, *, bounds=None, k=0, precision="mixed",
     d.jacobi_tol = float(jacobi_tol)
     d.refine_iters = int(refine_iters)
     d.flags = int(flags)
+    d.merge_arity = int(merge_arity)
+    d.merge_rank = int(merge_rank)
     return d, keep
 
 
@@ -324,6 +328,40 @@ def right_vectors_static(M, N, col_ptr, row_idx, vals, sigma, U, V, *, k=None, r
            _ptr(sigma), _ptr(U), float(rank_tol), _ptr(patches), _ptr(npatches), int(max_patches),
            vv, _ptr(V), _stream_handle(stream))
     _check(st, "svd_right_vectors_static")
+
+
+PRODUCT_SYM = 1
+PRODUCT_LEGACY_MMA = 2
+
+
+def exact_product(A, B=None, *, slices=5, legacy=False, out=None, err=None, stream=None):
+    """C = A B^T (B = A when None: symmetric, upper tiles mirrored) for FP64
+    device tensors, through svd_exact_product: exact 8-bit slices on the bf16
+    tensor cores (tcgen05 with TMEM accumulators, or mma.sync when legacy).
+    The workspace is a torch allocation; err, when given, is a device int32
+    tensor that a timed-out wait sets to 1."""
+    import torch
+    lib = load_library()
+    f = lib.svd_exact_product
+    if f.argtypes is None:
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        f.argtypes = [I32, I32, I64, P, I64, P, I64, P, I64, I32, I32, P, ctypes.c_size_t, P, P]
+        f.restype = I32
+        g = lib.svd_exact_product_bytes
+        g.argtypes = [I32, I32, I64, I32]
+        g.restype = ctypes.c_size_t
+    sym = B is None
+    m, k = A.shape
+    n = m if sym else B.shape[0]
+    nbytes = lib.svd_exact_product_bytes(m, n, k, slices)
+    work = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=A.device)
+    C = torch.empty(m, n, dtype=torch.float64, device=A.device) if out is None else out
+    flags = (PRODUCT_SYM if sym else 0) | (PRODUCT_LEGACY_MMA if legacy else 0)
+    st = f(m, n, k, _ptr(A), A.stride(0), None if sym else _ptr(B), 0 if sym else B.stride(0),
+           _ptr(C), C.stride(0), slices, flags, _ptr(work), int(nbytes), _ptr(err),
+           _stream_handle(stream))
+    _check(st, "svd_exact_product")
+    return C
 
 
 class SvdIo(ctypes.Structure):

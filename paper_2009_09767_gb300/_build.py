@@ -12,7 +12,7 @@ OUT = os.path.join(HERE, "libranky.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
 SOURCES = ["partition.cu", "gram.cu", "jacobi.cu", "dense.cu", "spmm.cu", "ozaki.cu", "api.cu",
            "transpose.cu",
-           "static_scratch.cu", "server.cpp"]
+           "static_scratch.cu", "cluster_rr.cu", "ozaki_tc.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -37,12 +37,16 @@ struct svd_plan_s {
     bool patched = false;   // any insertion mode
     bool tall = false;      // SVD_FLAG_TALL: the caller's CSC is this problem's transpose
     double jac_tol = 0.0;
-    int max_sweeps = 40, refine_iters = 1, merge_refine_iters = 3;
+    int max_sweeps = 40, refine_iters = 2, merge_refine_iters = 3;
+    double rr_kappa = 32.0;    // Rayleigh-Ritz clusters: first-order mixing estimate >= 1 / rr_kappa
     std::vector<int64_t> bounds_h;
     int nchunks = 0;
     int W = 0;  // bitmap words per block
     int nsplit = 1;
     int64_t Rmax = 0;
+    int arity = 0;          // tree merge: children per node (>= 2), 0 = one-level merge
+    int keep = 0;           // k' > 0: directions a block / node passes upward
+    int Dcap = 0;           // D rounded up to a multiple of the arity (tree scratch)
 
     char* arena = nullptr;
     size_t arena_bytes = 0;
@@ -113,7 +117,13 @@ struct svd_plan_s {
     double* W64 = nullptr;
     float* W32 = nullptr;
     int32_t* sweeps = nullptr;
-    int32_t* scratch_flag = nullptr;
+    int32_t* dev_err = nullptr;  // [0]: a bounded wait of the tcgen05 products ran out
+    // cluster Rayleigh-Ritz of the refinement (mixed): D blocks, then the merge
+    int32_t* rr_order = nullptr;
+    int32_t* rr_cstart = nullptr;
+    int32_t* rr_csize = nullptr;
+    int32_t* rr_ncl = nullptr;
+    int32_t* rr_cid = nullptr;
 
     // svd_run_host staging (lazily allocated)
     char* host_arena = nullptr;
@@ -182,6 +192,11 @@ svd_status validate_short_fat(const svd_desc* d) {
     const int64_t kmax = std::min<int64_t>(d->M, d->N);
     if (d->k > kmax) return SVD_ERR_INVALID_ARG;
     if (d->M > kMaxM) return SVD_ERR_UNSUPPORTED;
+    if (d->merge_arity < 0 || d->merge_rank < 0) return SVD_ERR_INVALID_ARG;
+    if (d->merge_rank > 0) {
+        const int64_t k = d->k > 0 ? d->k : kmax;
+        if (d->merge_rank < k) return SVD_ERR_INVALID_ARG;
+    }
     if (d->block_col_bounds) {
         const int64_t* b = d->block_col_bounds;
         if (b[0] != 0 || b[d->num_blocks] != d->N) return SVD_ERR_INVALID_ARG;
@@ -227,16 +242,16 @@ void carve(svd_plan_s* p, Carver& c) {
         p->G32 = c.take<float>((size_t)D * mm);
         p->Vt32 = c.take<float>((size_t)D * mm);
         p->jwork = c.take<char>(jacobi_work_bytes(D + 1, Mp));
-        if (p->refine_iters > 0) {
+        if (p->refine_iters > 0 || p->arity) {
             p->Xn = c.take<double>((size_t)D * mm);
             p->RW1 = c.take<double>((size_t)D * mm);
-            p->RW2 = c.take<double>((size_t)D * mm);
+            p->RW2 = c.take<double>((size_t)std::max(D, p->Dcap) * mm);   // + tree scratch Y
             p->RW3 = c.take<double>((size_t)D * mm);
             p->lam = c.take<double>((size_t)D * Mp);
             p->norms = c.take<double>(D);
         }
     } else {
-        p->Gw64 = c.take<double>((size_t)D * mm);
+        p->Gw64 = c.take<double>((size_t)std::max(D, p->Dcap) * mm);   // + tree scratch Y
     }
     p->bsig = c.take<double>((size_t)D * M);
     p->bperm = c.take<int32_t>((size_t)D * M);
@@ -261,7 +276,8 @@ void carve(svd_plan_s* p, Carver& c) {
         p->W64 = c.take<double>((size_t)M * std::max(p->k, 1));
     }
     if (p->use_oz) {
-        const int64_t blk = p->refine_iters > 0 ? oz_operand_elems(D, 5, Mp, Mp) : 0;
+        const int64_t blk = (p->refine_iters > 0 || p->arity)
+                                ? oz_operand_elems(std::max(D, p->Dcap), 5, Mp, Mp) : 0;
         const int64_t mrg = std::max(oz_operand_elems(1, 5, M, p->Rmax), oz_operand_elems(1, 5, Mp, Mp));
         const int64_t rows = round_up(Mp, OZ_ROW_PAD);
         p->oz_sl[0] = c.take<uint16_t>((size_t)std::max(blk, mrg));
@@ -272,8 +288,24 @@ void carve(svd_plan_s* p, Carver& c) {
     p->msig = c.take<double>(M);
     p->mperm = c.take<int32_t>(M);
     p->mrank = c.take<int32_t>(1);
-    p->sweeps = c.take<int32_t>(D + 1);
-    p->scratch_flag = c.take<int32_t>(4);
+    p->sweeps = c.take<int32_t>(D + 1 + (p->arity ? D : 0));   // blocks, merge, tree nodes
+    p->dev_err = c.take<int32_t>(4);
+    if (p->mixed) {
+        p->rr_order = c.take<int32_t>((size_t)(D + 1) * Mp);
+        p->rr_cstart = c.take<int32_t>((size_t)(D + 1) * (Mp / 2));
+        p->rr_csize = c.take<int32_t>((size_t)(D + 1) * (Mp / 2));
+        p->rr_ncl = c.take<int32_t>(D + 1);
+        p->rr_cid = c.take<int32_t>((size_t)(D + 1) * Mp);
+    }
+}
+
+// Cluster Rayleigh-Ritz work of matrix `first` onwards (the D blocks from 0,
+// the merge at D).
+RRWork rr_work(svd_plan_s* p, int first) {
+    const int Mp = p->Mp;
+    return RRWork{p->rr_order + (size_t)first * Mp, p->rr_cstart + (size_t)first * (Mp / 2),
+                  p->rr_csize + (size_t)first * (Mp / 2), p->rr_ncl + first,
+                  p->rr_cid + (size_t)first * Mp, p->rr_kappa, p->M};
 }
 
 svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
@@ -294,7 +326,7 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
     p->W = (d->M + 31) / 32;
     p->max_sweeps = d->max_sweeps > 0 ? d->max_sweeps : 40;
     p->jac_tol = d->jacobi_tol > 0 ? d->jacobi_tol : (p->mixed ? 8.0 * Eps<float>::value : 1e-14);
-    p->refine_iters = d->refine_iters >= 0 ? d->refine_iters : 1;
+    p->refine_iters = d->refine_iters >= 0 ? d->refine_iters : 2;
     p->bounds_h.resize(p->D + 1);
     if (d->block_col_bounds) {
         std::copy(d->block_col_bounds, d->block_col_bounds + p->D + 1, p->bounds_h.begin());
@@ -308,10 +340,17 @@ svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
         nch += ceil_div(p->bounds_h[i + 1] - p->bounds_h[i], kChunkCols);
     if (nch > (int64_t)1 << 30) return SVD_ERR_UNSUPPORTED;
     p->nchunks = (int)nch;
+    p->arity = d->merge_arity >= 2 ? d->merge_arity : 0;
+    p->keep = d->merge_rank;
+    p->Dcap = p->arity ? (int)round_up(p->D, p->arity) : p->D;
     int64_t rmax = 0;
-    for (int i = 0; i < p->D; ++i)
-        rmax += std::min<int64_t>(p->M, p->bounds_h[i + 1] - p->bounds_h[i]);
-    p->Rmax = std::max<int64_t>(rmax, 1);
+    for (int i = 0; i < p->D; ++i) {
+        int64_t r = std::min<int64_t>(p->M, p->bounds_h[i + 1] - p->bounds_h[i]);
+        if (p->keep > 0) r = std::min<int64_t>(r, p->keep);
+        rmax += r;
+    }
+    // the tree merge never forms the proxy P
+    p->Rmax = p->arity ? 1 : std::max<int64_t>(rmax, 1);
     p->nsplit = merge_gram_splits(p->M, p->Rmax);
     return SVD_OK;
 }
@@ -442,14 +481,71 @@ svd_status block_jacobi(svd_plan_s* p, cudaStream_t s) {
 // Kernels one refinement step launches (see launch_refine): the sparse
 // route adds the transpose of X and the scatter, the exact-slice products
 // two kernels per operand split.
-int refine_launches(bool sparse, bool oz, int nchunks) {
+int refine_launches(bool sparse, bool oz, int nchunks, bool rr) {
     const int scatter = sparse && nchunks > 0 ? 1 : 0;
-    if (oz) return sparse ? 15 + scatter : 16;
-    return sparse ? 7 + scatter : 7;
+    const int extra = rr ? 3 : 0;   // five kernels in place of the two of the norm-threshold step
+    if (oz) return (sparse ? 15 + scatter : 17) + extra;
+    return (sparse ? 7 + scatter : 7) + extra;
 }
 
 void oz_ops(svd_plan_s* p, OzOperand* ops) {
-    for (int i = 0; i < 2; ++i) ops[i] = OzOperand{p->oz_sl[i], p->oz_amax[i], 0, 0, 0, 0};
+    const int tc = (p->d.flags & SVD_FLAG_LEGACY_MMA) ? 0 : 1;
+    for (int i = 0; i < 2; ++i)
+        ops[i] = OzOperand{p->oz_sl[i], p->oz_amax[i], 0, 0, 0, 0, tc, p->dev_err};
+}
+
+// The tree merge (merge_arity >= 2): every level forms the node matrices
+// S_node = sum over the node's children of Y_c^T Y_c (Y_c = S_c U_c^T, the
+// child's proxy columns as rows), eigensolves them as the blocks were
+// (mixed: FP32 Jacobi + refinement; FP64: FP64 Jacobi), sorts and ranks
+// them, and passes their bases up; the root's matrix goes to S64 for the
+// merge eigensolve.  X: the blocks' eigenvector rows (FP64).
+svd_status tree_merge(svd_plan_s* p, const double* X, OzOperand* oz, cudaStream_t s) {
+    const int D = p->D, M = p->M, Mp = p->Mp, a = p->arity;
+    const int64_t mm = (int64_t)Mp * Mp;
+    int n = D, node_off = 0;
+    for (;;) {
+        const int nn = (int)ceil_div(n, a);
+        double* Y = p->mixed ? p->RW2 : p->Gw64;
+        LAUNCH(p, p->use_oz ? 4 : 2,
+               launch_tree_level(X, p->bsig, p->bperm, p->brank, n, a, M, Mp, p->keep, Y,
+                                 nn == 1 ? p->S64 : p->G64, p->use_oz ? oz : nullptr, s));
+        if (nn == 1) break;
+        int32_t* sw = p->sweeps + D + 1 + node_off;
+        if (!p->mixed) {
+            CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * nn * mm, cudaMemcpyDeviceToDevice, s));
+            LAUNCH(p, 1, launch_jacobi<double>(p->Gw64, p->Vt64, nn, Mp, p->max_sweeps, p->jac_tol,
+                                               sw, s));
+            LAUNCH(p, 1, launch_sort_rank(nullptr, nullptr, p->Gw64, nullptr, nn, M, Mp, nullptr, p->N,
+                                          p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
+            X = p->Vt64;
+        } else {
+            LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, nn * mm, s));
+            LAUNCH(p, 1, launch_jacobi<float>(p->G32, p->Vt32, nn, Mp, p->max_sweeps, p->jac_tol, sw,
+                                              s, p->jwork));
+            LAUNCH(p, 1, launch_convert_f32_f64(p->Vt32, p->Vt64, nn * mm, s));
+            double* Xc = p->Vt64;
+            double* Xn = p->Xn;
+            const RRWork rr = rr_work(p, 0);
+            const bool use_rr = p->rr_kappa > 0;
+            for (int it = 0; it < p->refine_iters; ++it) {
+                LAUNCH(p, refine_launches(false, p->use_oz, 0, use_rr),
+                       launch_refine(p->G64, Xc, Xn, p->lam, nn, Mp, p->RW1, p->RW2, p->RW3, p->norms,
+                                     s, nullptr, p->use_oz ? oz : nullptr, use_rr ? &rr : nullptr));
+                std::swap(Xc, Xn);
+            }
+            if (p->refine_iters > 0)
+                LAUNCH(p, 1, launch_sort_rank(p->lam, nullptr, nullptr, nullptr, nn, M, Mp, nullptr,
+                                              p->N, p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
+            else
+                LAUNCH(p, 1, launch_sort_rank(nullptr, nullptr, nullptr, p->G32, nn, M, Mp, nullptr,
+                                              p->N, p->d.rank_tol, p->bsig, p->bperm, p->brank, s));
+            X = Xc;
+        }
+        node_off += nn;
+        n = nn;
+    }
+    return SVD_OK;
 }
 
 // Block refinement, sort and rank, proxy P and P P^T (Eqs. 2-3); leaves the
@@ -481,11 +577,13 @@ svd_status phase_mid(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
                               p->chunk_block, p->chunk_lo, p->chunk_hi};
         OzOperand oz[2];
         oz_ops(p, oz);
+        const RRWork rr = rr_work(p, 0);
+        const bool use_rr = p->rr_kappa > 0;
         for (int it = 0; it < p->refine_iters; ++it) {
-            LAUNCH(p, refine_launches(sparse, p->use_oz, p->nchunks),
+            LAUNCH(p, refine_launches(sparse, p->use_oz, p->nchunks, use_rr),
                    launch_refine(p->G64, X, Xn, p->lam, D, Mp, p->RW1, p->RW2, p->RW3,
                                        p->norms, s, sparse ? &sb : nullptr,
-                                       p->use_oz ? oz : nullptr));
+                                       p->use_oz ? oz : nullptr, use_rr ? &rr : nullptr));
             std::swap(X, Xn);
         }
         LAUNCH(p, 1, launch_sort_rank(p->lam, nullptr, nullptr, nullptr, D, M, Mp, p->bounds_d, 0,
@@ -497,13 +595,23 @@ svd_status phase_mid(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         Xblk32 = p->Vt32;
     }
     mark(p, 4, s);
-    LAUNCH(p, 2, launch_proxy(Xblk64, Xblk32, p->bsig, p->bperm, p->brank, D, M, Mp, p->pofs, p->P,
-                              s));
-    mark(p, 5, s);
     OzOperand oz[2];
     oz_ops(p, oz);
-    LAUNCH(p, p->use_oz ? 4 : 2, launch_merge_gram(p->P, p->pofs, D, M, Mp, p->Rmax, p->partial, p->nsplit,
-                                   p->S64, s, p->use_oz ? oz : nullptr));
+    if (!p->arity) {
+        LAUNCH(p, 2, launch_proxy(Xblk64, Xblk32, p->bsig, p->bperm, p->brank, D, M, Mp, p->pofs,
+                                  p->P, s, p->keep));
+        mark(p, 5, s);
+        LAUNCH(p, p->use_oz ? 4 : 2, launch_merge_gram(p->P, p->pofs, D, M, Mp, p->Rmax, p->partial, p->nsplit,
+                                       p->S64, s, p->use_oz ? oz : nullptr));
+    } else {
+        mark(p, 5, s);
+        if (!Xblk64) {   // FP32 bases (no refinement): the tree works on FP64 rows
+            LAUNCH(p, 1, launch_convert_f32_f64(p->Vt32, p->Vt64, (int64_t)D * mm, s));
+            Xblk64 = p->Vt64;
+        }
+        svd_status st = tree_merge(p, Xblk64, oz, s);
+        if (st != SVD_OK) return st;
+    }
     mark(p, 6, s);
     if (!p->mixed)
         CU(cudaMemcpyAsync(p->Sw64, p->S64, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
@@ -539,10 +647,13 @@ svd_status phase_post(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         double* Xn = p->SXn;
         OzOperand oz[2];
         oz_ops(p, oz);
+        const RRWork rr = rr_work(p, D);
+        const bool use_rr = p->rr_kappa > 0;
         for (int it = 0; it < p->merge_refine_iters; ++it) {
-            LAUNCH(p, refine_launches(false, p->use_oz, 0),
+            LAUNCH(p, refine_launches(false, p->use_oz, 0, use_rr),
                    launch_refine(p->S64, X, Xn, p->slam, 1, Mp, p->SR1, p->SR2, p->SR3,
-                                       p->snorm, s, nullptr, p->use_oz ? oz : nullptr));
+                                       p->snorm, s, nullptr, p->use_oz ? oz : nullptr,
+                                       use_rr ? &rr : nullptr));
             std::swap(X, Xn);
         }
         LAUNCH(p, 1, launch_sort_rank(p->slam, nullptr, nullptr, nullptr, 1, M, Mp, nullptr, p->N,
@@ -595,6 +706,54 @@ svd_status run_device(svd_plan_s* p, const int64_t* col_ptr, const int32_t* row_
 extern "C" {
 
 int32_t svd_version(void) { return 1; }
+
+namespace {
+// workspace of svd_exact_product: the two operands' slices and row bounds
+struct ProductLayout {
+    size_t a_sl, b_sl, a_mx, b_mx, total;
+};
+ProductLayout product_layout(int32_t m, int32_t n, int64_t k, int32_t S, bool sym) {
+    ProductLayout L{};
+    const size_t ea = (size_t)oz_operand_elems(1, S, m, k) * sizeof(uint16_t);
+    const size_t eb = sym ? 0 : (size_t)oz_operand_elems(1, S, n, k) * sizeof(uint16_t);
+    L.a_sl = 0;
+    L.b_sl = align_up(ea);
+    L.a_mx = L.b_sl + align_up(eb);
+    L.b_mx = L.a_mx + align_up(sizeof(unsigned long long) * round_up(m, OZ_ROW_PAD));
+    L.total = L.b_mx + align_up(sizeof(unsigned long long) * round_up(n, OZ_ROW_PAD));
+    return L;
+}
+}  // namespace
+
+size_t svd_exact_product_bytes(int32_t m, int32_t n, int64_t k, int32_t slices) {
+    if (m < 1 || n < 1 || k < 1 || (slices != 3 && slices != 5)) return 0;
+    return product_layout(m, n, k, slices, false).total;
+}
+
+svd_status svd_exact_product(int32_t m, int32_t n, int64_t k, const double* d_A, int64_t lda,
+                             const double* d_B, int64_t ldb, double* d_C, int64_t ldc,
+                             int32_t slices, int32_t flags, void* d_work, size_t work_bytes,
+                             int32_t* d_err, void* stream) {
+    const bool sym = (flags & SVD_PRODUCT_SYM) != 0;
+    if (m < 1 || n < 1 || k < 1 || m > (1 << 20) || n > (1 << 20)) return SVD_ERR_INVALID_ARG;
+    if (slices != 3 && slices != 5) return SVD_ERR_INVALID_ARG;
+    if (sym && n != m) return SVD_ERR_INVALID_ARG;
+    if (!d_A || (!sym && !d_B) || !d_C || !d_work || lda < k || (!sym && ldb < k) || ldc < n)
+        return SVD_ERR_INVALID_ARG;
+    const ProductLayout L = product_layout(m, n, k, slices, sym);
+    if (work_bytes < L.total) return SVD_ERR_INVALID_ARG;
+    char* w = static_cast<char*>(d_work);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int tc = (flags & SVD_PRODUCT_LEGACY_MMA) ? 0 : 1;
+    OzOperand a{reinterpret_cast<uint16_t*>(w + L.a_sl), reinterpret_cast<unsigned long long*>(w + L.a_mx),
+                0, 0, 0, 0, tc, d_err};
+    OzOperand b{reinterpret_cast<uint16_t*>(w + L.b_sl), reinterpret_cast<unsigned long long*>(w + L.b_mx),
+                0, 0, 0, 0, tc, d_err};
+    CU(launch_oz_split(1, m, k, d_A, lda, 0, 0, nullptr, slices, a, s));
+    if (!sym) CU(launch_oz_split(1, n, k, d_B, ldb, 0, 0, nullptr, slices, b, s));
+    CU(launch_oz_gemm(1, m, n, a, sym ? a : b, 1.0, 0.0, d_C, ldc, 0, sym ? 1 : 0, s));
+    return SVD_OK;
+}
 
 const char* svd_status_str(svd_status s) {
     switch (s) {
@@ -673,7 +832,9 @@ svd_status plan_create(const svd_desc* desc, void* arena, size_t arena_bytes, sv
                           cudaMemcpyHostToDevice) == cudaSuccess;
     ok = ok && cudaMemcpy(p->chunk_hi, chi.data(), sizeof(int64_t) * chi.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && cudaMemset(p->sweeps, 0, sizeof(int32_t) * (p->D + 1)) == cudaSuccess;
+    ok = ok && cudaMemset(p->sweeps, 0, sizeof(int32_t) * (p->D + 1 + (p->arity ? p->D : 0))) ==
+                   cudaSuccess;
+    ok = ok && cudaMemset(p->dev_err, 0, sizeof(int32_t) * 4) == cudaSuccess;
     if (!ok) {
         if (p->owns_arena) cudaFree(p->arena);
         delete p;
@@ -820,8 +981,12 @@ svd_status svd_sync(svd_plan_t p) {
     if (!p) return SVD_ERR_INVALID_ARG;
     if (!p->ran) return SVD_OK;
     if (p->last_stream) CU(cudaStreamSynchronize(p->last_stream));
-    std::vector<int32_t> sw(p->D + 1);
-    CU(cudaMemcpy(sw.data(), p->sweeps, sizeof(int32_t) * (p->D + 1), cudaMemcpyDeviceToHost));
+    const int nsw = p->D + 1 + (p->arity ? p->D : 0);
+    std::vector<int32_t> sw(nsw);
+    CU(cudaMemcpy(sw.data(), p->sweeps, sizeof(int32_t) * nsw, cudaMemcpyDeviceToHost));
+    int32_t err = 0;
+    CU(cudaMemcpy(&err, p->dev_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (err) return SVD_ERR_TIMEOUT;
     for (int32_t v : sw)
         if (v < 0) return SVD_ERR_NOT_CONVERGED;
     return SVD_OK;
@@ -886,9 +1051,14 @@ svd_status svd_query(svd_plan_t p, int32_t what, int64_t index, void* h_dst, siz
         }
         case SVD_Q_PROXY_COLS:
             if (bytes != sizeof(int64_t)) return SVD_ERR_INVALID_ARG;
+            if (p->arity) {   // the tree merge forms no proxy
+                memset(h_dst, 0, bytes);
+                return SVD_OK;
+            }
             CU(cudaMemcpy(h_dst, p->pofs + D, bytes, cudaMemcpyDeviceToHost));
             return SVD_OK;
         case SVD_Q_PROXY: {
+            if (p->arity) return SVD_ERR_UNSUPPORTED;
             int64_t R = 0;
             CU(cudaMemcpy(&R, p->pofs + D, sizeof(int64_t), cudaMemcpyDeviceToHost));
             if (bytes != sizeof(double) * M * R) return SVD_ERR_INVALID_ARG;
@@ -1085,6 +1255,8 @@ svd_status batch_engine_assign(svd_batch_t b, int n, const svd_plan_t* plans, cu
     // work lists: [blocks f32 | blocks f64 | merges f32 | merges f64]
     std::vector<JacobiItem> lists[4];
     const int cap32 = jacobi_item_max_mp(false), cap64 = jacobi_item_max_mp(true);
+    for (int i = 0; i < n; ++i)
+        if (plans[i] && plans[i]->arity) return SVD_ERR_UNSUPPORTED;   // tree merges run alone
     for (int i = 0; i < n; ++i) {
         svd_plan_s* p = plans[i];
         const bool f64 = !p->mixed;
@@ -1101,6 +1273,7 @@ svd_status batch_engine_assign(svd_batch_t b, int n, const svd_plan_t* plans, cu
             it.sweeps = p->sweeps + d;
             it.work = f64 ? nullptr : (void*)(p->jwork + jacobi_work_bytes(d, p->Mp));
             it.Mp = p->Mp;
+            it.max_sweeps = p->max_sweeps;
             lists[wb].push_back(it);
         }
         JacobiItem m{};
@@ -1109,6 +1282,7 @@ svd_status batch_engine_assign(svd_batch_t b, int n, const svd_plan_t* plans, cu
         m.sweeps = p->sweeps + p->D;
         m.work = f64 ? nullptr : (void*)(p->jwork + jacobi_work_bytes(p->D, p->Mp));
         m.Mp = p->Mp;
+        m.max_sweeps = p->max_sweeps;
         lists[2 + wb].push_back(m);
         for (int w : {wb, 2 + wb}) {
             b->maxmp[w] = std::max(b->maxmp[w], p->Mp);
@@ -1162,7 +1336,7 @@ svd_status svd_batch_create(int32_t n, const svd_plan_t* plans, int32_t flags, s
     for (int i = 0; i < n; ++i)
         if (!plans[i]) return SVD_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i)
-        if (plans[i]->tall) return SVD_ERR_UNSUPPORTED;
+        if (plans[i]->tall || plans[i]->arity) return SVD_ERR_UNSUPPORTED;
     size_t items = 0;
     for (int i = 0; i < n; ++i) items += (size_t)plans[i]->D + 1;
     svd_batch_t b = nullptr;

@@ -312,9 +312,10 @@ k_sparse_gxt(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ ro
 }
 }  // namespace
 
-cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* lam, int nmat,
+cudaError_t launch_refine(const double* G, double* X, double* Xn, double* lam, int nmat,
                           int Mp, double* W1, double* W2, double* W3, double* norms,
-                          cudaStream_t s, const SparseBlocks* sp, OzOperand* oz) {
+                          cudaStream_t s, const SparseBlocks* sp, OzOperand* oz,
+                          const RRWork* rr) {
     const int64_t st = (int64_t)Mp * Mp;
     if (sp) {
         // X^T staged in W3 for the sparse product
@@ -365,7 +366,12 @@ cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* 
             RK_CUDA_TRY(launch_dgemm(nmat, Mp, Mp, Mp, 1.0, W2, Mp, st, 0, X, Mp, st, 1, 0.0, W3, Mp, st, s, 1));
         }
     }
-    {
+    if (rr) {
+        // estimates, clusters, Rayleigh-Ritz inside them (X, S (W3), X X^T
+        // (W1) and lam in place; W2, dead after the products, holds the
+        // cluster rotations), then E over W1
+        RK_CUDA_TRY(launch_cluster_rr(*rr, nmat, Mp, X, W3, W1, W2, lam, norms, s));
+    } else {
         // cluster size: enough CTAs to cover the GPU, a divisor of Mp, <= 16
         int cs = 1;
         while (cs < 16 && nmat * cs < 304 && Mp % (2 * cs) == 0) cs *= 2;
@@ -384,10 +390,10 @@ cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* 
         cfg.numAttrs = 1;
         RK_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_oa_norms, (const double*)W1, (const double*)W3, Mp, cs,
                                        lam, norms));
+        const int bx = (int)std::min<int64_t>(ceil_div(st, 256), 1024);
+        k_oa_E<<<dim3(bx, nmat), 256, 0, s>>>(W1, W3, Mp, lam, norms);
+        RK_CUDA_TRY(cudaGetLastError());
     }
-    const int bx = (int)std::min<int64_t>(ceil_div(st, 256), 1024);
-    k_oa_E<<<dim3(bx, nmat), 256, 0, s>>>(W1, W3, Mp, lam, norms);
-    RK_CUDA_TRY(cudaGetLastError());
     // Xn = X + E^T X
     RK_CUDA_TRY(cudaMemcpyAsync(Xn, X, sizeof(double) * st * nmat, cudaMemcpyDeviceToDevice, s));
     if (oz) {
@@ -482,20 +488,24 @@ cudaError_t launch_sort_rank(const double* lam, const float* lam32, const double
 // ---------------------------------------------------------------------------
 // Proxy P = [U^1[:, :r_1] S^1 | ... ], column-major M x R with R = sum r_i.
 namespace {
-__global__ void k_proxy_ofs(const int32_t* __restrict__ rank, int D, int64_t* __restrict__ ofs) {
+__global__ void k_proxy_ofs(const int32_t* __restrict__ rank, int D, int keep_max,
+                            int64_t* __restrict__ ofs) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int64_t acc = 0;
-        for (int d = 0; d < D; ++d) { ofs[d] = acc; acc += rank[d]; }
+        for (int d = 0; d < D; ++d) {
+            ofs[d] = acc;
+            acc += keep_max > 0 ? min(rank[d], keep_max) : rank[d];
+        }
         ofs[D] = acc;
     }
 }
 
 __global__ void k_proxy(const double* __restrict__ X64, const float* __restrict__ X32,
                         const double* __restrict__ sigma_sorted, const int32_t* __restrict__ perm,
-                        const int32_t* __restrict__ rank, int M, int Mp,
+                        const int32_t* __restrict__ rank, int M, int Mp, int keep_max,
                         const int64_t* __restrict__ ofs, double* __restrict__ P) {
     const int d = blockIdx.y;
-    const int r = rank[d];
+    const int r = keep_max > 0 ? min(rank[d], keep_max) : rank[d];
     const int64_t base = ofs[d];
     const int64_t mo = (int64_t)d * Mp * Mp;
     for (int j = blockIdx.x; j < r; j += gridDim.x) {
@@ -512,12 +522,61 @@ __global__ void k_proxy(const double* __restrict__ X64, const float* __restrict_
 
 cudaError_t launch_proxy(const double* X64, const float* X32, const double* sigma_sorted,
                          const int32_t* perm, const int32_t* rank, int D, int M, int Mp,
-                         int64_t* proxy_ofs, double* P, cudaStream_t s) {
-    k_proxy_ofs<<<1, 32, 0, s>>>(rank, D, proxy_ofs);
+                         int64_t* proxy_ofs, double* P, cudaStream_t s, int keep_max) {
+    k_proxy_ofs<<<1, 32, 0, s>>>(rank, D, keep_max, proxy_ofs);
     RK_CUDA_TRY(cudaGetLastError());
     const int bx = M < 64 ? M : 64;
-    k_proxy<<<dim3(bx, D), 128, 0, s>>>(X64, X32, sigma_sorted, perm, rank, M, Mp, proxy_ofs, P);
+    k_proxy<<<dim3(bx, D), 128, 0, s>>>(X64, X32, sigma_sorted, perm, rank, M, Mp, keep_max,
+                                        proxy_ofs, P);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One level of the tree merge: the weighted bases Y_c (Mp x Mp, row j =
+// sigma_cj times the eigenvector of the j-th largest eigenvalue of child c,
+// for j below the child's kept rank; zero otherwise, and for the padding
+// children c >= nchild), then S_node = sum over its `arity` consecutive
+// children of Y_c^T Y_c (the children's proxy columns are the rows of Y_c:
+// S_node = P_node P_node^T, Eq. 3, without forming P).
+namespace {
+__global__ void k_tree_weights(const double* __restrict__ X64, const double* __restrict__ sigma_sorted,
+                               const int32_t* __restrict__ perm, const int32_t* __restrict__ rank,
+                               int nchild, int M, int Mp, int keep_max, double* __restrict__ Y) {
+    const int c = blockIdx.y;
+    const int64_t mm = (int64_t)Mp * Mp;
+    double* Yc = Y + (int64_t)c * mm;
+    int kept = 0;
+    if (c < nchild) kept = keep_max > 0 ? min(rank[c], keep_max) : rank[c];
+    for (int j = blockIdx.x; j < Mp; j += gridDim.x) {
+        double sg = 0.0;
+        const double* x = nullptr;
+        if (j < kept) {
+            sg = sigma_sorted[(int64_t)c * M + j];
+            x = X64 + (int64_t)c * mm + (int64_t)perm[(int64_t)c * M + j] * Mp;
+        }
+        for (int m = threadIdx.x; m < Mp; m += blockDim.x)
+            Yc[(int64_t)j * Mp + m] = (x && m < M) ? sg * x[m] : 0.0;
+    }
+}
+}  // namespace
+
+cudaError_t launch_tree_level(const double* X64, const double* sigma_sorted, const int32_t* perm,
+                              const int32_t* rank, int nchild, int arity, int M, int Mp,
+                              int keep_max, double* Y, double* S, OzOperand* oz, cudaStream_t s) {
+    const int nnode = (int)ceil_div(nchild, arity);
+    const int64_t mm = (int64_t)Mp * Mp;
+    k_tree_weights<<<dim3(std::min(Mp, 128), nnode * arity), 128, 0, s>>>(
+        X64, sigma_sorted, perm, rank, nchild, M, Mp, keep_max, Y);
+    RK_CUDA_TRY(cudaGetLastError());
+    const int64_t k = (int64_t)arity * Mp;
+    if (oz) {
+        // A = the stacked Y of a node read transposed: Mp rows (coordinates) x
+        // arity Mp k (the children's proxy columns)
+        RK_CUDA_TRY(launch_oz_split(nnode, Mp, k, Y, Mp, arity * mm, 1, nullptr, 5, oz[0], s));
+        return launch_oz_gemm(nnode, Mp, Mp, oz[0], oz[0], 1.0, 0.0, S, Mp, mm, 1, s);
+    }
+    return launch_dgemm(nnode, Mp, Mp, (int)k, 1.0, Y, Mp, arity * mm, 1, Y, Mp, arity * mm, 0,
+                        0.0, S, Mp, mm, s, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -496,7 +496,8 @@ k_jacobi_items(const JacobiItem* __restrict__ items, int nitems, int* __restrict
         const JacobiItem w = items[it];
         const int ppc = w.Mp / kB2;
         jacobi_matrix<T, false>(static_cast<T*>(w.G), static_cast<T*>(w.Vt), w.Mp, 1, 0, ppc,
-                                max_sweeps, tol, w.sweeps, smem_raw);
+                                w.max_sweeps > 0 ? w.max_sweeps : max_sweeps, tol, w.sweeps,
+                                smem_raw);
         __syncthreads();
     }
 }
@@ -928,8 +929,9 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     }
     __syncthreads();
     const float sc = scale_sh;
-    // absolute floor of the rotation threshold (see the FP64 solver)
-    const float floor_abs = 4.f * (float)Eps<float>::value * dmax_sh;
+    // absolute floor of the rotation threshold (see the FP64 solver): half the
+    // relative threshold, times the largest diagonal (4 eps at the default)
+    const float floor_abs = 0.5f * tol * dmax_sh;
     owner_sync<kCluster>();
     for (int64_t e = (int64_t)crank * kJT4 + threadIdx.x; e < (int64_t)Mp * Mp;
          e += (int64_t)csize * kJT4) {
@@ -1084,7 +1086,8 @@ k_jacobi4_items(const JacobiItem* __restrict__ items, int nitems, int* __restric
         if (it >= nitems) break;
         const JacobiItem w = items[it];
         jacobi4_matrix<false>(static_cast<float*>(w.G), static_cast<float*>(w.Vt), w.Mp, 1, 0,
-                              max_sweeps, tol, w.sweeps, static_cast<uint32_t*>(w.work), smem_raw);
+                              w.max_sweeps > 0 ? w.max_sweeps : max_sweeps, tol, w.sweeps,
+                              static_cast<uint32_t*>(w.work), smem_raw);
         __syncthreads();
     }
 }

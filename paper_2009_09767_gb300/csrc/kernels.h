@@ -73,7 +73,7 @@ struct JacobiItem {
     int32_t* sweeps;
     void* work;        // FP32: jacobi_work_bytes(1, Mp) bytes
     int32_t Mp;
-    int32_t pad;
+    int32_t max_sweeps;  // this matrix's sweep cap (> 0; else the launch's)
 };
 // Largest Mp one persistent worker CTA can hold.
 int jacobi_item_max_mp(bool fp64);
@@ -101,6 +101,8 @@ struct OzOperand {
     int rows;
     int rows_pad;
     int64_t kpad;
+    int tc = 1;                      // products on tcgen05/TMEM (ozaki_tc.cu), else mma.sync
+    int* err = nullptr;              // device word set when a bounded wait of the tcgen05 kernel ran out
 };
 int64_t oz_operand_elems(int nb, int S, int rows, int64_t k);
 // Split nb matrices (rows x k logical; element (r, c) at src[r ld + c], or at
@@ -116,6 +118,12 @@ cudaError_t launch_oz_split(int nb, int rows, int64_t k, const double* src, int6
 cudaError_t launch_oz_gemm(int nb, int m, int n, const OzOperand& A, const OzOperand& B,
                            double alpha, double beta, double* C, int64_t ldc, int64_t strideC,
                            int sym, cudaStream_t s, int nsplit = 1, int64_t strideSplit = 0);
+// The same product with tcgen05.mma (accumulators in TMEM); bit for bit the
+// result of the mma.sync kernel.  err (may be null) is set to 1 when a
+// bounded wait ran out (the CTA then stops without writing its tile).
+cudaError_t launch_oz_gemm_tc(int nb, int m, int n, const OzOperand& A, const OzOperand& B,
+                              double alpha, double beta, double* C, int64_t ldc, int64_t strideC,
+                              int sym, cudaStream_t s, int nsplit, int64_t strideSplit, int* err);
 // The sparse blocks behind block cross products (for G X^T without the dense G).
 struct SparseBlocks {
     const int64_t* col_ptr;
@@ -133,10 +141,31 @@ struct SparseBlocks {
 // With sp, G X^T is formed from the sparse columns (G itself unused); with
 // oz (two operand buffers of nmat x 5 slices x Mp x Mp) every product runs on
 // the tensor cores through exact slices instead of the FP64 pipes.
-cudaError_t launch_refine(const double* G, const double* X, double* Xn, double* lam, int nmat,
+// Cluster Rayleigh-Ritz work (cluster_rr.cu): per matrix the sorted member
+// order (Mp), cluster starts and sizes (Mp/2 each) and the cluster count.
+struct RRWork {
+    int32_t* order;
+    int32_t* cstart;
+    int32_t* csize;
+    int32_t* ncl;
+    int32_t* cid;      // per matrix, Mp: cluster of each index (-1: none)
+    double kappa;      // pairs whose first-order mixing estimate is >= 1/kappa are clustered
+    int M;             // indices >= M are padding and never clustered
+};
+// With rr, the rows of each cluster of strongly mixed estimates are first
+// replaced by the Ritz vectors of the projected problem (X is updated in
+// place, and S, X X^T and lam with it), then every other pair takes the
+// first-order correction (the published step's cluster threshold and its
+// norm estimates are not used).
+cudaError_t launch_refine(const double* G, double* X, double* Xn, double* lam, int nmat,
                           int Mp, double* W1, double* W2, double* W3, double* norms,
                           cudaStream_t s, const SparseBlocks* sp = nullptr,
-                          OzOperand* oz = nullptr);
+                          OzOperand* oz = nullptr, const RRWork* rr = nullptr);
+// Estimates, clusters, Rayleigh-Ritz and the correction E written over B
+// (five kernels); Tg is Mp x Mp scratch per matrix, lmax one double per matrix.
+cudaError_t launch_cluster_rr(const RRWork& w, int nmat, int Mp, double* X, double* S, double* B,
+                              double* Tg, double* lam, double* lmax, cudaStream_t s);
+size_t rr_smem_bytes();
 // Per matrix: sort eigenvalues (lam, or the diagonal of Gdiag when lam is null)
 // of the first M indices descending, rank by tolerance, write sigma
 // (sqrt(max(lam,0))) sorted, the permutation and the rank.
@@ -145,9 +174,19 @@ cudaError_t launch_sort_rank(const double* lam, const float* lam32, const double
                              const float* diag32, int nmat, int M, int Mp, const int64_t* bounds,
                              int64_t width_all, double rank_tol, double* sigma_sorted,
                              int32_t* perm, int32_t* rank, cudaStream_t s);
+// keep_max > 0: at most that many columns per block (the truncation k').
 cudaError_t launch_proxy(const double* X64, const float* X32, const double* sigma_sorted,
                          const int32_t* perm, const int32_t* rank, int D, int M, int Mp,
-                         int64_t* proxy_ofs, double* P, cudaStream_t s);
+                         int64_t* proxy_ofs, double* P, cudaStream_t s, int keep_max = 0);
+// One tree-merge level: nchild children (eigenvector rows X64, sorted sigma,
+// permutation, rank, as launch_sort_rank leaves them) -> ceil(nchild / arity)
+// node matrices S (Mp x Mp each).  Y holds ceil(nchild / arity) * arity
+// Mp x Mp matrices of scratch; with oz, the products are exact-slice ones
+// (oz[0] must hold nnode x 5 slices of Mp x arity Mp), else FP64.  Two or
+// four kernels.
+cudaError_t launch_tree_level(const double* X64, const double* sigma_sorted, const int32_t* perm,
+                              const int32_t* rank, int nchild, int arity, int M, int Mp,
+                              int keep_max, double* Y, double* S, OzOperand* oz, cudaStream_t s);
 // S = P P^T (M x M, stored Mp x Mp), split over the R columns.
 cudaError_t launch_merge_gram(const double* P, const int64_t* proxy_ofs, int D, int M, int Mp,
                               int64_t Rmax, double* partial, int nsplit, double* S, cudaStream_t s,

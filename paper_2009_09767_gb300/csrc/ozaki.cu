@@ -404,6 +404,9 @@ cudaError_t launch_oz_gemm(int nb, int m, int n, const OzOperand& A, const OzOpe
         return cudaErrorInvalidValue;
     if (sym && m != n) return cudaErrorInvalidValue;
     if (nb <= 0 || m <= 0 || n <= 0) return cudaSuccess;
+    if (A.tc)
+        return launch_oz_gemm_tc(nb, m, n, A, B, alpha, beta, C, ldc, strideC, sym, s, nsplit,
+                                 strideSplit, A.err);
     if (A.S == 3)
         return oz_gemm_t<3>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
                             strideSplit, sym, s);

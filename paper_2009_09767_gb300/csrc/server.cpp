@@ -297,7 +297,7 @@ void release(svd_server_s* s, Request* r) {
 
 bool small_request(const Request* r) {
     return r->desc.M <= kSmallM && r->desc.num_blocks <= kSmallBlocks && !r->inject_alloc &&
-           !r->inject_bad_csc;
+           !r->inject_bad_csc && r->desc.merge_arity <= 1;
 }
 
 void scheduler(svd_server_s* s) {

@@ -69,3 +69,50 @@ def subspace_check(X, X_ref, s_ref, tol, gap=1e-3, floor=1e-8):
 def orthonormality(X):
     X = np.asarray(X, dtype=np.float64)
     return float(np.abs(X.T @ X - np.eye(X.shape[1])).max())
+
+
+def sparse_csc(col_ptr, row_idx, vals, M):
+    """scipy CSC matrix of the input (test-side products at full size)."""
+    import scipy.sparse as sp
+    N = len(col_ptr) - 1
+    return sp.csc_matrix((np.asarray(vals, dtype=np.float64), np.asarray(row_idx),
+                          np.asarray(col_ptr)), shape=(M, N))
+
+
+def gram_angle_bounds(A, s, U):
+    """Davis-Kahan bounds on the angle between each computed u_i and the true
+    eigenvector of A A^T: r_i = |A A^T u_i - s_i^2 u_i| (FP64 sparse products),
+    every true eigenvalue lies within r_j of some s_j^2, so the separation of
+    s_i^2 from the other true eigenvalues is at least
+    g_i = min_{j != i} |s_i^2 - s_j^2| - r_i - max_j r_j, and
+    sin(angle_i) <= r_i / g_i (inf where g_i <= 0)."""
+    U = np.asarray(U, dtype=np.float64)
+    lam = np.asarray(s, dtype=np.float64) ** 2
+    r = np.zeros(len(lam))
+    for c0 in range(0, len(lam), 64):
+        Uc = U[:, c0:c0 + 64]
+        R = A @ (A.T @ Uc) - Uc * lam[None, c0:c0 + 64]
+        r[c0:c0 + 64] = np.linalg.norm(R, axis=0)
+    out = np.full(len(lam), np.inf)
+    rmax = float(r.max())
+    for i in range(len(lam)):
+        d = np.abs(lam - lam[i])
+        d[i] = np.inf
+        g = float(d.min()) - r[i] - rmax
+        if g > 0:
+            out[i] = r[i] / g
+    return out, r
+
+
+def separated(s, gap=1e-3):
+    """Indices whose sigma is at least gap * sigma_1 from both neighbours."""
+    s = np.asarray(s, dtype=np.float64)
+    s1 = float(s[0])
+    keep = []
+    for i in range(len(s)):
+        if i > 0 and s[i - 1] - s[i] < gap * s1:
+            continue
+        if i + 1 < len(s) and s[i] - s[i + 1] < gap * s1:
+            continue
+        keep.append(i)
+    return np.asarray(keep, dtype=np.int64)

@@ -20,17 +20,15 @@ Reported per (density, blocks, rank fix, precision):
 The dataset is missing, so the values are not comparable to the paper's
 tables.
 
-Asserted:
-- FP64: sigma within 1e-6 relative, angles within 1e-4, eigen-residual within 1e-11.
-- Mixed: sigma within 1e-4 relative and the eigen-residual within 1e-5.
-  The residual bounds the backward error, not the angle. With one
-  refinement step of each block basis, the mixed path leaves a backward
-  error of a few 1e-6 sigma_1^2 on dense blocks (the table: up to 5e-6):
-  pairs of block eigenvalues closer than the first step's cluster threshold
-  keep the mixing of the FP32 solve. A vector whose squared singular value
-  is isolated by only a few 1e-4 sigma_1^2 can then be off by more than
-  1e-4 in angle (the table reports up to ~5e-4 at density 0.0005 with 2-16
-  blocks).
+Asserted, for both precisions:
+- sigma within 1e-6 (FP64) / 1e-4 (mixed) relative;
+- the largest principal-angle sine within 1e-4 (projectors inside sigma
+  clusters), the stated tolerance of both modes;
+- the eigen-residual within 1e-11 (FP64) / 1e-8 (mixed) of sigma_1^2.
+The mixed mode meets the angle bound on the dense blocks of these patterns
+(many close or exactly repeated block eigenvalues) through the Rayleigh-Ritz
+rotation inside clusters of strongly mixed pairs in each of its two
+refinement steps; a first-order step alone left angles up to 5e-4 here.
 Every case runs before the assertions, so one run prints the whole table.
 """
 import dataclasses
@@ -52,7 +50,8 @@ DENSITIES = (0.0005, 0.002)
 MODES = ("truncate", "random", "neighbor", "neighbor_random")
 SEED = 170897
 TOL = {"fp64": 1e-6, "mixed": 1e-4}
-RESID_TOL = {"fp64": 1e-11, "mixed": 1e-5}
+RESID_TOL = {"fp64": 1e-11, "mixed": 1e-8}
+ANGLE_TOL = 1e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -131,7 +130,7 @@ def test_paper_tables_synthetic(density):
                     failures.append((tag, f"sigma relative error {rel:.2e}"))
                 if resid > RESID_TOL[prec]:
                     failures.append((tag, f"eigen-residual {resid:.2e}"))
-                if prec == "fp64" and ang > 1e-4:
+                if ang > ANGLE_TOL:
                     failures.append((tag, f"angle {ang:.2e}"))
                 lines.append(f"| {density:g} | {D} | 539 x {int(np.diff(b)[0])} | {mode} | "
                              f"{int(fix.sum())} | {len(expect[mode])} | {prec} | {e_s:.3e} | "

@@ -82,3 +82,34 @@ def test_static_right_vectors_rejects_oversize():
     st = f(1024, 1024, 0, 1, P(cp), None, None, 1024, None, P(dummy), 0.0, None, None, 0, 0,
            P(dummy), None)
     assert st == 1
+
+
+@pytest.mark.parametrize("precision,k", [("mixed", 101), ("mixed", 100), ("fp64", 37)])
+def test_static_right_vectors_top_k(precision, k):
+    """Top-k calls: k < M, and k % 4 != 0 (the FP32 scalar SpMM path).  From
+    the same sigma and U, the static entry's V equals svd_run's V of a top-k
+    plan, and the first k columns of a full plan's V."""
+    assert torch.cuda.is_available()
+    dev = torch.device("cuda")
+    case = _case("wide512")
+    cp = torch.from_numpy(case.col_ptr).to(dev)
+    ri = torch.from_numpy(case.row_idx).to(dev)
+    va = torch.from_numpy(case.vals).to(dev)
+    tol = 1e-6 if precision == "mixed" else 1e-12
+    for kk in (k, None):
+        plan = rk.Plan(case.M, case.N, case.nnz, case.num_blocks, value_type="f32",
+                       precision=precision, k=kk or 0)
+        o = rk.alloc_outputs(plan, device=dev)
+        plan.run(cp, ri, va, o["sigma"], o["U"], o["V"], o["rank"], o["patches"], o["npatches"])
+        plan.sync()
+        V_ref = o["V"][:, :k]
+        sig = o["sigma"][:k].contiguous()
+        U = o["U"][:k].contiguous()          # k x M rows = column-major M x k
+        scale = float(V_ref.abs().max())
+        for call in range(2):
+            V = torch.full((case.N, k), float("nan"), dtype=V_ref.dtype, device=dev)
+            rk.right_vectors_static(case.M, case.N, cp, ri, va, sig, U, V, k=k)
+            torch.cuda.synchronize()
+            assert not torch.isnan(V).any(), (kk, call)
+            assert float((V - V_ref).abs().max()) <= tol * scale, (kk, call)
+        plan.free()
