@@ -551,10 +551,10 @@ def main():
                     help="zipf_wide: skip the plain FP64 arm (same matrix, --precision fp64)")
     ap.add_argument("--no-serve", action="store_true",
                     help="zipf_wide: skip the bounded serving sweep")
-    ap.add_argument("--serve-rates", default="mixed:100,mixed:500,fp64:100",
+    ap.add_argument("--serve-rates", default="mixed:100,mixed:400,fp64:100",
                     help="zipf_wide: serving sweep as precision:rate pairs")
-    ap.add_argument("--serve-duration", type=float, default=3.0)
-    ap.add_argument("--serve-grace", type=float, default=3.0)
+    ap.add_argument("--serve-duration", type=float, default=2.0)
+    ap.add_argument("--serve-grace", type=float, default=2.0)
     args = ap.parse_args()
 
     if args.impl == "reference":

@@ -145,6 +145,10 @@ typedef struct {
                                  warp-level mma.sync tensor path instead of tcgen05.mma
                                  with TMEM accumulators (bit-identical results; for
                                  testing and timing) */
+#define SVD_FLAG_ATOMIC_GRAM 128 /* form the block cross products with global FP64 atomics
+                                 (plus separate mirror and conversion passes) instead of
+                                 the thread-block-cluster form (same values up to the
+                                 summation order; for testing and timing) */
 #define SVD_FLAG_TALL 32       /* tall-and-skinny A: M rows (any, >= 1) and N <= 1024
                                  columns, split into num_blocks ROW blocks (the row-block
                                  form of section II); block_col_bounds then holds D+1

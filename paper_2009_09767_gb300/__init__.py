@@ -37,6 +37,7 @@ FLAG_DENSE_REFINE = 8
 FLAG_FP64_PRODUCTS = 16
 FLAG_TALL = 32
 FLAG_LEGACY_MMA = 64
+FLAG_ATOMIC_GRAM = 128
 STAGES = ["partition", "gram", "block_jacobi", "block_refine", "sort_proxy", "merge_gram",
           "merge_eig", "finalize", "spmm"]
 

@@ -305,7 +305,7 @@ RRWork rr_work(svd_plan_s* p, int first) {
     const int Mp = p->Mp;
     return RRWork{p->rr_order + (size_t)first * Mp, p->rr_cstart + (size_t)first * (Mp / 2),
                   p->rr_csize + (size_t)first * (Mp / 2), p->rr_ncl + first,
-                  p->rr_cid + (size_t)first * Mp, p->rr_kappa, p->M};
+                  p->rr_cid + (size_t)first * Mp, p->rr_kappa, p->M, 0};
 }
 
 svd_status fill_plan(const svd_desc* d, svd_plan_s* p) {
@@ -435,7 +435,6 @@ svd_status phase_pre(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
                                           M, p->nnz, p->t_cnt, p->t_tile, p->t_tmp_idx,
                                           p->t_tmp_val, p->t_ptr, p->t_idx, p->t_val, s));
     CU(cudaMemsetAsync(p->occ, 0, sizeof(uint32_t) * (size_t)D * p->W, s));
-    CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
     LAUNCH(p, 1, launch_occupancy(io.col_ptr, io.row_idx, io.vals, vt, M, p->nchunks,
                                   p->chunk_block, p->chunk_lo, p->chunk_hi, p->occ, s));
     PatchRec* ext = reinterpret_cast<PatchRec*>(io.patches);
@@ -454,17 +453,31 @@ svd_status phase_pre(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
                                              p->patch_ofs, ext, io.npatches, s));
     }
     mark(p, 1, s);
-    LAUNCH(p, 1, launch_gram(io.col_ptr, io.row_idx, io.vals, vt, Mp, p->nchunks, p->chunk_block,
-                             p->chunk_lo, p->chunk_hi, p->G64, s));
-    if (p->patched)
-        LAUNCH(p, 1, launch_gram_patches(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->patches,
-                                         p->patch_ofs, D * M, p->G64, s));
-    LAUNCH(p, 1, launch_symmetrize(p->G64, D, Mp, s));
+    // without insertions: the cluster form writes the full matrices and the
+    // solver's copy in one pass; with insertions (added by atomics to the
+    // upper triangle), or where clusters cannot run, the atomic form
+    bool done = false;
+    if (!p->patched && !(p->d.flags & SVD_FLAG_ATOMIC_GRAM)) {
+        CU(launch_gram_cluster(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->bounds_d, p->G64,
+                               p->mixed ? p->G32 : nullptr, p->mixed ? nullptr : p->Gw64, s, &done));
+        if (done) ++p->launches;
+    }
+    if (!done) {
+        CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
+        LAUNCH(p, 1, launch_gram(io.col_ptr, io.row_idx, io.vals, vt, Mp, p->nchunks, p->chunk_block,
+                                 p->chunk_lo, p->chunk_hi, p->G64, s));
+        if (p->patched)
+            LAUNCH(p, 1, launch_gram_patches(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->patches,
+                                             p->patch_ofs, D * M, p->G64, s));
+        LAUNCH(p, 1, launch_symmetrize(p->G64, D, Mp, s));
+    }
     mark(p, 2, s);
-    if (!p->mixed)
-        CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * D * mm, cudaMemcpyDeviceToDevice, s));
-    else
-        LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, (int64_t)D * mm, s));
+    if (!done) {
+        if (!p->mixed)
+            CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * D * mm, cudaMemcpyDeviceToDevice, s));
+        else
+            LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, (int64_t)D * mm, s));
+    }
     return SVD_OK;
 }
 
@@ -526,9 +539,10 @@ svd_status tree_merge(svd_plan_s* p, const double* X, OzOperand* oz, cudaStream_
             LAUNCH(p, 1, launch_convert_f32_f64(p->Vt32, p->Vt64, nn * mm, s));
             double* Xc = p->Vt64;
             double* Xn = p->Xn;
-            const RRWork rr = rr_work(p, 0);
+            RRWork rr = rr_work(p, 0);
             const bool use_rr = p->rr_kappa > 0;
             for (int it = 0; it < p->refine_iters; ++it) {
+                rr.stagger = it & 1;
                 LAUNCH(p, refine_launches(false, p->use_oz, 0, use_rr),
                        launch_refine(p->G64, Xc, Xn, p->lam, nn, Mp, p->RW1, p->RW2, p->RW3, p->norms,
                                      s, nullptr, p->use_oz ? oz : nullptr, use_rr ? &rr : nullptr));
@@ -577,9 +591,10 @@ svd_status phase_mid(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
                               p->chunk_block, p->chunk_lo, p->chunk_hi};
         OzOperand oz[2];
         oz_ops(p, oz);
-        const RRWork rr = rr_work(p, 0);
+        RRWork rr = rr_work(p, 0);
         const bool use_rr = p->rr_kappa > 0;
         for (int it = 0; it < p->refine_iters; ++it) {
+            rr.stagger = it & 1;
             LAUNCH(p, refine_launches(sparse, p->use_oz, p->nchunks, use_rr),
                    launch_refine(p->G64, X, Xn, p->lam, D, Mp, p->RW1, p->RW2, p->RW3,
                                        p->norms, s, sparse ? &sb : nullptr,
@@ -647,9 +662,10 @@ svd_status phase_post(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
         double* Xn = p->SXn;
         OzOperand oz[2];
         oz_ops(p, oz);
-        const RRWork rr = rr_work(p, D);
+        RRWork rr = rr_work(p, D);
         const bool use_rr = p->rr_kappa > 0;
         for (int it = 0; it < p->merge_refine_iters; ++it) {
+            rr.stagger = it & 1;
             LAUNCH(p, refine_launches(false, p->use_oz, 0, use_rr),
                    launch_refine(p->S64, X, Xn, p->slam, 1, Mp, p->SR1, p->SR2, p->SR3,
                                        p->snorm, s, nullptr, p->use_oz ? oz : nullptr,

@@ -43,7 +43,7 @@ namespace rk {
 
 namespace {
 
-constexpr int kRRMax = 64;              // largest cluster solved exactly
+constexpr int kRRMax = 96;              // largest cluster solved exactly (3 x 96 x 97 doubles of shared memory)
 constexpr int kRRLd = kRRMax + 1;       // odd stride: row and column access conflict-free
 constexpr int kRRSweeps = 30;           // Jacobi sweep cap inside a cluster
 constexpr int kRRSlots = 16;            // CTAs per matrix walking the cluster list
@@ -72,9 +72,9 @@ __device__ __forceinline__ void rr_pair(int n, int r, int u, int& a, int& b) {
 // One CTA of 1024 threads per matrix (Mp <= 1024).
 __global__ void __launch_bounds__(1024)
 k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp, double kappa,
-          double* __restrict__ lam, double* __restrict__ lmax_out, int32_t* __restrict__ order,
-          int32_t* __restrict__ cstart, int32_t* __restrict__ csize, int32_t* __restrict__ ncl,
-          int32_t* __restrict__ cid) {
+          int stagger, double* __restrict__ lam, double* __restrict__ lmax_out,
+          int32_t* __restrict__ order, int32_t* __restrict__ cstart, int32_t* __restrict__ csize,
+          int32_t* __restrict__ ncl, int32_t* __restrict__ cid) {
     __shared__ double key[kMaxM];
     __shared__ int id[kMaxM];
     __shared__ int reach[kMaxM];
@@ -176,17 +176,20 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         while (i < M) {
             int j = i, end = reach[i];
             while (j < end) { ++j; end = max(end, reach[j]); }
-            // run [i, end]; longer than kRRMax: cut at the largest gap among
-            // positions i + kRRMax/4 .. i + kRRMax - 1
+            // run [i, end]; longer than kRRMax: pieces of nominal length kRRMax
+            // (the first one half as long when staggered), each cut at the
+            // largest gap in the last quarter of its nominal span
+            int len = stagger ? kRRMax / 2 : kRRMax;
             while (end - i + 1 > kRRMax) {
-                int best = i + kRRMax - 1;
+                int best = i + len - 1;
                 double bg = -1.0;
-                for (int q = i + kRRMax / 4; q < i + kRRMax - 1; ++q) {
+                for (int q = i + len - kRRMax / 4; q < i + len - 1; ++q) {
                     const double g = key[q + 1] - key[q];
                     if (g > bg) { bg = g; best = q; }
                 }
                 emit(i, best);
                 i = best + 1;
+                len = kRRMax;
             }
             emit(i, end);
             i = end + 1;
@@ -379,8 +382,9 @@ k_rr_rows(double* __restrict__ Z0, double* __restrict__ Z1, double* __restrict__
           const int32_t* __restrict__ order, const int32_t* __restrict__ cstart,
           const int32_t* __restrict__ csize, const int32_t* __restrict__ ncl,
           const double* __restrict__ Tg) {
-    __shared__ double Ts[kRRMax][kRRLd];
-    __shared__ double buf[kRRMax][kRRTile + 1];
+    extern __shared__ double rr_dyn[];
+    double (*Ts)[kRRLd] = reinterpret_cast<double (*)[kRRLd]>(rr_dyn);
+    double (*buf)[kRRTile + 1] = reinterpret_cast<double (*)[kRRTile + 1]>(rr_dyn + kRRMax * kRRLd);
     __shared__ int ix[kRRMax];
     const int b = blockIdx.z, c0 = blockIdx.x * kRRTile, tid = threadIdx.x;
     const int half = Mp / 2;
@@ -424,8 +428,9 @@ k_rr_cols(double* __restrict__ Z0, double* __restrict__ Z1, int Mp,
           const int32_t* __restrict__ order, const int32_t* __restrict__ cstart,
           const int32_t* __restrict__ csize, const int32_t* __restrict__ ncl,
           const double* __restrict__ Tg) {
-    __shared__ double Ts[kRRMax][kRRLd];
-    __shared__ double buf[kRRTile][kRRMax + 1];
+    extern __shared__ double rr_dyn[];
+    double (*Ts)[kRRLd] = reinterpret_cast<double (*)[kRRLd]>(rr_dyn);
+    double (*buf)[kRRMax + 1] = reinterpret_cast<double (*)[kRRMax + 1]>(rr_dyn + kRRMax * kRRLd);
     __shared__ int ix[kRRMax];
     const int b = blockIdx.z, r0 = blockIdx.x * kRRTile, tid = threadIdx.x;
     const int half = Mp / 2;
@@ -503,19 +508,23 @@ cudaError_t launch_cluster_rr(const RRWork& w, int nmat, int Mp, double* X, doub
                               double* Tg, double* lam, double* lmax, cudaStream_t s) {
     if (nmat <= 0) return cudaSuccess;
     if (Mp > kMaxM || Mp % kRRTile != 0 || w.M > Mp) return cudaErrorInvalidValue;
-    k_rr_plan<<<nmat, 1024, 0, s>>>(S, B, w.M, Mp, w.kappa, lam, lmax, w.order, w.cstart,
-                                    w.csize, w.ncl, w.cid);
+    k_rr_plan<<<nmat, 1024, 0, s>>>(S, B, w.M, Mp, w.kappa, w.stagger, lam, lmax, w.order,
+                                    w.cstart, w.csize, w.ncl, w.cid);
     RK_CUDA_TRY(cudaGetLastError());
     const int smem = (int)rr_smem_bytes();
     RK_CUDA_TRY(cudaFuncSetAttribute(k_rr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_rr_solve<<<dim3(kRRSlots, nmat), 256, smem, s>>>(S, B, Mp, w.order, w.cstart, w.csize, w.ncl,
                                                       Tg, lam);
     RK_CUDA_TRY(cudaGetLastError());
-    k_rr_rows<<<dim3(Mp / kRRTile, kRRSlots, nmat), 256, 0, s>>>(X, S, B, Mp, w.order, w.cstart,
-                                                                w.csize, w.ncl, Tg);
+    const int srow = (int)(sizeof(double) * (kRRMax * kRRLd + kRRMax * (kRRTile + 1)));
+    const int scol = (int)(sizeof(double) * (kRRMax * kRRLd + kRRTile * (kRRMax + 1)));
+    RK_CUDA_TRY(cudaFuncSetAttribute(k_rr_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, srow));
+    RK_CUDA_TRY(cudaFuncSetAttribute(k_rr_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, scol));
+    k_rr_rows<<<dim3(Mp / kRRTile, kRRSlots, nmat), 256, srow, s>>>(X, S, B, Mp, w.order, w.cstart,
+                                                                   w.csize, w.ncl, Tg);
     RK_CUDA_TRY(cudaGetLastError());
-    k_rr_cols<<<dim3(Mp / kRRTile, kRRSlots, nmat), 256, 0, s>>>(S, B, Mp, w.order, w.cstart,
-                                                                w.csize, w.ncl, Tg);
+    k_rr_cols<<<dim3(Mp / kRRTile, kRRSlots, nmat), 256, scol, s>>>(S, B, Mp, w.order, w.cstart,
+                                                                   w.csize, w.ncl, Tg);
     RK_CUDA_TRY(cudaGetLastError());
     const int bx = (int)std::min<int64_t>(ceil_div((int64_t)Mp * Mp, 256), 1024);
     k_rr_correction<<<dim3(bx, nmat), 256, 0, s>>>(B, S, Mp, lam, lmax, w.cid, 1.0 / w.kappa);

@@ -47,6 +47,15 @@ cudaError_t launch_gram(const int64_t* col_ptr, const int32_t* row_idx, const vo
 cudaError_t launch_gram_patches(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
                                 int value_type, int Mp, int D, const PatchRec* patches,
                                 const int64_t* patch_ofs, int max_patches, double* G, cudaStream_t s);
+// The same cross products formed in thread-block clusters (distributed shared
+// memory, one cluster per block and pass), written once as full symmetric
+// matrices G, and also converted into G32 (when G32 is given) or copied into
+// G64copy (when given); G needs no clearing.  bounds: D+1 column bounds on
+// the device.  *done = false when this device cannot run the cluster form
+// (nothing was enqueued; use launch_gram instead).
+cudaError_t launch_gram_cluster(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
+                                int value_type, int Mp, int D, const int64_t* bounds, double* G,
+                                float* G32, double* G64copy, cudaStream_t s, bool* done);
 // Mirror the upper triangle into the lower one, in place, for nmat matrices.
 cudaError_t launch_symmetrize(double* G, int nmat, int Mp, cudaStream_t s);
 cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
@@ -151,6 +160,7 @@ struct RRWork {
     int32_t* cid;      // per matrix, Mp: cluster of each index (-1: none)
     double kappa;      // pairs whose first-order mixing estimate is >= 1/kappa are clustered
     int M;             // indices >= M are padding and never clustered
+    int stagger = 0;   // odd refinement steps: long runs are cut half a piece later
 };
 // With rr, the rows of each cluster of strongly mixed estimates are first
 // replaced by the Ritz vectors of the projected problem (X is updated in

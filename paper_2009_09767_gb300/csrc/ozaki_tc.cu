@@ -1,6 +1,7 @@
 // ozaki_tc.cu -- the exact-slice FP64-accurate product (see ozaki.cu for the
-// splitting) on the fifth-generation tensor cores: tcgen05.mma with operands
-// in shared memory and FP32 accumulators in tensor memory (TMEM).
+// splitting) on the fifth-generation tensor cores: operands brought into
+// shared memory by the tensor memory accelerator (cp.async.bulk.tensor, 128-
+// byte swizzle), tcgen05.mma with FP32 accumulators in tensor memory (TMEM).
 //
 // C = alpha A B^T (+ beta C) from the S bf16 slices of A (m rows) and B
 // (n rows).  Every slice pair (a, b) with a + b <= S + 1 gets its own TMEM
@@ -13,14 +14,19 @@
 //
 // CTA: 128 threads, output tile 128 x 32 (row i of the tile = TMEM lane i =
 // thread i at the drain), S (S + 1) / 2 <= 15 accumulators of 32 columns in
-// one 512-column TMEM allocation.  k runs in stages of 64 through two shared
-// buffers (cp.async, canonical no-swizzle K-major layout: 8-row x 16-byte
-// core matrices, 128 bytes apart along k and 1024 bytes apart along rows);
-// thread 0 issues the stage's MMAs (M = 128, N = 32, K = 16) and commits
-// them to the buffer's mbarrier, which the loads of the stage two ahead wait
-// on.  Every wait is bounded: on expiry the CTA records an error, lets its
-// copies land, frees its TMEM and returns.
+// one 512-column TMEM allocation.  k runs in stages of 64 through NBUF shared
+// buffers; one thread issues each stage's tensor copies (one per slice and
+// operand, completion counted in bytes on the buffer's "full" mbarrier) and,
+// once they have landed, the stage's MMAs (M = 128, N = 32, K = 16), which it
+// commits to the buffer's "empty" mbarrier before refilling the buffer.
+// Shared tiles are K-major with the 128-byte swizzle: rows of 64 bf16, 8-row
+// atoms of 1024 bytes; along k inside an atom the descriptor start advances
+// by 32 bytes per MMA.  Every wait is bounded: on expiry the CTA records an
+// error, lets what it issued land (bounded), frees its TMEM and returns.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -33,29 +39,33 @@ constexpr int TBM = 128, TBN = 32, TBK = 64;
 constexpr int kDrainK = 1024;                       // exact run of one accumulator
 constexpr int kStagesPerDrain = kDrainK / TBK;
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitLimit = 1ll << 24;         // try_wait polls before giving up
+constexpr long long kWaitCycles = 1ll << 31;        // ~1 s of SM clock before a wait gives up
 
 template <int S>
 struct TcSmem {
-    static constexpr int A_BYTES = TBM * TBK * 2;    // one slice, 16 KB
+    static constexpr int A_BYTES = TBM * TBK * 2;    // one slice tile, 16 KB
     static constexpr int B_BYTES = TBN * TBK * 2;    // 4 KB
     static constexpr int STAGE = S * (A_BYTES + B_BYTES);
-    static constexpr int BYTES = 2 * STAGE + 128;    // + mbarriers and the TMEM address
+    static constexpr int NBUF = S <= 3 ? 3 : 2;
+    static constexpr int BAR = NBUF * STAGE;         // barriers after the buffers
+    static constexpr int BYTES = BAR + 256 + 1024;   // + barriers, TMEM slot, alignment slack
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor, no swizzle, K-major: start, leading byte
-// offset (next core matrix along k), stride byte offset (next 8 rows)
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 bytes apart (stride byte offset); the leading byte offset is unused
+// for this layout (encoded 1)
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of this architecture
-    return d;                 // base offset 0, layout type 0 (no swizzle)
+    d |= (uint64_t)1 << 16;                     // leading byte offset (16 B, unused)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version of this architecture
+    d |= (uint64_t)2 << 61;                     // layout: 128-byte swizzle
+    return d;
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
@@ -80,6 +90,11 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -91,15 +106,29 @@ __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait for the phase of the given parity; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
+// bounded wait for the phase of the given parity; false when about a second
+// of SM clock passed or (when given) the CTA's failure flag was raised
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          const volatile int* failed = nullptr) {
+    const long long t0 = clock64();
+    for (unsigned i = 0;; ++i) {
         if (mbar_test(mbar, parity)) return true;
-    return false;
+        if ((i & 63) == 63) {
+            if (clock64() - t0 > kWaitCycles) return false;
+            if (failed && *failed) return false;
+        }
+    }
 }
 
-__device__ __forceinline__ void cp16(uint32_t saddr, const void* g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g));
+// 3-d tensor copy global -> shared (coordinates k, row, slice), completion
+// counted on mbar
+__device__ __forceinline__ void tma_load(uint32_t sdst, const CUtensorMap* map, int x, int y, int z,
+                                         uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sdst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -121,34 +150,29 @@ __device__ __forceinline__ int tc_exp(unsigned long long bits) {
     return (ef == 0 ? 1 : ef) - 1022;
 }
 
-// byte offset of (row r, 16-byte chunk c along k) in a tile of the canonical layout
-__device__ __forceinline__ uint32_t core_off(int r, int c) {
-    return (uint32_t)((r >> 3) * 1024 + c * 128 + (r & 7) * 16);
-}
-
 template <int S>
 __global__ void __launch_bounds__(128, 1)
-k_oz_umma(int m, int n, int64_t kpad, int64_t kc, const uint16_t* __restrict__ As,
-          const unsigned long long* __restrict__ amaxA, int rowsA_pad,
-          const uint16_t* __restrict__ Bs, const unsigned long long* __restrict__ amaxB,
-          int rowsB_pad, double alpha, double beta, double* __restrict__ C, int64_t ldc,
-          int64_t strideC, int64_t strideSplit, int nsplit, int sym, int* __restrict__ err) {
-    constexpr int NP = S * (S + 1) / 2;
-    static_assert(NP * TBN <= (int)kTmemCols, "accumulators exceed the TMEM allocation");
+k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m,
+          int n, int64_t kpad, int64_t kc, const unsigned long long* __restrict__ amaxA,
+          int rowsA_pad, const unsigned long long* __restrict__ amaxB, int rowsB_pad,
+          double alpha, double beta, double* __restrict__ C, int64_t ldc, int64_t strideC,
+          int64_t strideSplit, int nsplit, int sym, int* __restrict__ err) {
+    using L = TcSmem<S>;
+    constexpr int NB = L::NBUF;
     const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
     if (sym && j0 + TBN - 1 < i0) return;   // below the diagonal: mirrored from above
     const int b = blockIdx.z / nsplit, split = blockIdx.z % nsplit;
     const int64_t kb = (int64_t)split * kc;
     const int64_t ke = min(kpad, kb + kc);
-    extern __shared__ __align__(1024) unsigned char tc_sm[];
-    const uint32_t sbase = smem_u32(tc_sm);
-    const uint32_t mbar0 = sbase + 2 * TcSmem<S>::STAGE;   // two 8-byte mbarriers
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_sm + 2 * TcSmem<S>::STAGE + 16);
+    extern __shared__ unsigned char tc_sm[];
+    const uint32_t sraw = smem_u32(tc_sm);
+    const uint32_t sbase = (sraw + 1023u) & ~1023u;          // swizzle atoms want 1024-byte alignment
+    const uint32_t full0 = sbase + L::BAR;                     // NB "full" mbarriers
+    const uint32_t empty0 = full0 + 8 * NB;                    // NB "empty" mbarriers
+    const uint32_t drainb = empty0 + 8 * NB;                   // drain mbarrier
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_sm + (drainb + 8 - sraw));
     __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t sliceA = (int64_t)rowsA_pad * kpad, sliceB = (int64_t)rowsB_pad * kpad;
-    const uint16_t* Ab = As + (int64_t)b * S * sliceA + (int64_t)i0 * kpad;
-    const uint16_t* Bb = Bs + (int64_t)b * S * sliceB + (int64_t)j0 * kpad;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -158,9 +182,14 @@ k_oz_umma(int m, int n, int64_t kpad, int64_t kc, const uint16_t* __restrict__ A
     }
     if (tid == 0) {
         failed = 0;
-        mbar_init(mbar0, 1);
-        mbar_init(mbar0 + 8, 1);
+        for (int q = 0; q < NB; ++q) {
+            mbar_init(full0 + 8 * q, 1);
+            mbar_init(empty0 + 8 * q, 1);
+        }
+        mbar_init(drainb, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -171,107 +200,93 @@ k_oz_umma(int m, int n, int64_t kpad, int64_t kc, const uint16_t* __restrict__ A
 #pragma unroll
     for (int c = 0; c < TBN; ++c) acc[c] = 0;
 
-    // stage loads: A slices (TBM rows x TBK) then B slices (TBN rows x TBK),
-    // 16-byte chunks; k beyond ke reads as zero
-    auto load_stage = [&](int buf, int64_t k0) {
-        const uint32_t st = sbase + buf * TcSmem<S>::STAGE;
-        constexpr int CA = S * TBM * (TBK / 8), CB = S * TBN * (TBK / 8);
-        for (int q = tid; q < CA + CB; q += 128) {
-            int sl, r, ch;
-            uint32_t dst;
-            const uint16_t* src;
-            if (q < CA) {
-                sl = q / (TBM * (TBK / 8));
-                const int rem = q % (TBM * (TBK / 8));
-                r = rem / (TBK / 8);
-                ch = rem % (TBK / 8);
-                dst = st + sl * TcSmem<S>::A_BYTES + core_off(r, ch);
-                src = Ab + sl * sliceA + (int64_t)r * kpad + k0 + ch * 8;
-            } else {
-                const int qq = q - CA;
-                sl = qq / (TBN * (TBK / 8));
-                const int rem = qq % (TBN * (TBK / 8));
-                r = rem / (TBK / 8);
-                ch = rem % (TBK / 8);
-                dst = st + S * TcSmem<S>::A_BYTES + sl * TcSmem<S>::B_BYTES + core_off(r, ch);
-                src = Bb + sl * sliceB + (int64_t)r * kpad + k0 + ch * 8;
-            }
-            if (k0 + ch * 8 < ke) {
-                cp16(dst, src);
-            } else {
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(0u), "r"(0u),
-                             "r"(0u), "r"(0u));
-            }
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    };
-
-    // drain: every accumulator into the 64-bit sums (all 128 threads)
-    auto drain = [&]() {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        int p = 0;
-#pragma unroll 1
-        for (int a = 1; a <= S; ++a) {
-#pragma unroll 1
-            for (int bs = 1; a + bs <= S + 1; ++bs, ++p) {
-                uint32_t r[32];
-                tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * TBN), r);
-                const int sh = 8 * (S + 1 - a - bs);
-#pragma unroll
-                for (int c = 0; c < TBN; ++c)
-                    acc[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    };
-
     const int nst = (int)((ke - kb + TBK - 1) / TBK);
-    int last = -1;   // last stage whose MMAs were committed
-    for (int it = 0; it < nst; ++it) {
-        const int buf = it & 1;
-        if (it >= 2 && !mbar_wait(mbar0 + 8 * buf, (uint32_t)(((it - 2) >> 1) & 1))) {
-            failed = 1;
+    int issued = 0;        // stages whose copies thread 0 has issued
+    int committed = -1;    // last stage whose MMAs thread 0 has committed
+
+    // thread 0: the copies of stage st into buffer st % NB
+    auto issue_loads = [&](int st) {
+        const int buf = st % NB;
+        const uint32_t sb = sbase + buf * L::STAGE;
+        const uint32_t fb = full0 + 8 * buf;
+        mbar_expect_tx(fb, (uint32_t)L::STAGE);
+        const int x = (int)(kb + (int64_t)st * TBK);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+            tma_load(sb + sl * L::A_BYTES, &tmA, x, i0, b * S + sl, fb);
+            tma_load(sb + S * L::A_BYTES + sl * L::B_BYTES, &tmB, x, j0, b * S + sl, fb);
         }
+    };
+
+    int period = 0;
+    for (int p0 = 0; p0 < nst; p0 += kStagesPerDrain, ++period) {
+        const int p1 = min(nst, p0 + kStagesPerDrain);
+        if (tid == 0 && !failed) {
+            for (int st = p0; st < min(p1, p0 + NB); ++st) issue_loads(st);
+            issued = min(p1, p0 + NB);
+            for (int it = p0; it < p1; ++it) {
+                const int buf = it % NB;
+                const uint32_t par = (uint32_t)((it / NB) & 1);
+                if (!mbar_wait(full0 + 8 * buf, par)) { failed = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sb = sbase + buf * L::STAGE;
+                int p = 0;
+#pragma unroll 1
+                for (int a = 1; a <= S; ++a) {
+#pragma unroll 1
+                    for (int bs = 1; a + bs <= S + 1; ++bs, ++p) {
+                        const uint32_t sa = sb + (a - 1) * L::A_BYTES;
+                        const uint32_t sbb = sb + S * L::A_BYTES + (bs - 1) * L::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TBK / 16; ++kk)
+                            umma_bf16(tbase + (uint32_t)(p * TBN), umma_desc_sw128(sa + kk * 32),
+                                      umma_desc_sw128(sbb + kk * 32),
+                                      (it == p0 && kk == 0) ? 0u : 1u);
+                    }
+                }
+                umma_commit(empty0 + 8 * buf);
+                committed = it;
+                if (it + NB < p1) {
+                    // the buffer is refilled once the MMAs reading it are done
+                    if (!mbar_wait(empty0 + 8 * buf, par)) { failed = 1; break; }
+                    issue_loads(it + NB);
+                    issued = it + NB + 1;
+                }
+            }
+            if (!failed) umma_commit(drainb);
+        }
+        // drain: every thread, once the period's MMAs are done
+        if (!mbar_wait(drainb, (uint32_t)(period & 1), &failed)) failed = 1;
         __syncthreads();
         if (failed) break;
-        load_stage(buf, kb + (int64_t)it * TBK);
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = sbase + buf * TcSmem<S>::STAGE;
-            const bool first = (it % kStagesPerDrain) == 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        {
             int p = 0;
 #pragma unroll 1
             for (int a = 1; a <= S; ++a) {
 #pragma unroll 1
                 for (int bs = 1; a + bs <= S + 1; ++bs, ++p) {
-                    const uint32_t sa = st + (a - 1) * TcSmem<S>::A_BYTES;
-                    const uint32_t sb = st + S * TcSmem<S>::A_BYTES + (bs - 1) * TcSmem<S>::B_BYTES;
+                    uint32_t r[32];
+                    tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * TBN), r);
+                    const int sh = 8 * (S + 1 - a - bs);
 #pragma unroll
-                    for (int kk = 0; kk < TBK / 16; ++kk)
-                        umma_bf16(tbase + (uint32_t)(p * TBN), umma_desc(sa + kk * 256, 128, 1024),
-                                  umma_desc(sb + kk * 256, 128, 1024),
-                                  (first && kk == 0) ? 0u : 1u);
+                    for (int c = 0; c < TBN; ++c)
+                        acc[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
                 }
             }
-            umma_commit(mbar0 + 8 * buf);
         }
-        last = it;
-        if ((it % kStagesPerDrain) == kStagesPerDrain - 1 || it == nst - 1) {
-            if (!mbar_wait(mbar0 + 8 * buf, (uint32_t)((it >> 1) & 1))) failed = 1;
-            __syncthreads();
-            if (failed) break;
-            drain();
-            __syncthreads();
-        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
     }
     const bool ok = !failed;
+    if (!ok && tid == 0) {
+        // let what was issued land before the shared memory and TMEM go away
+        for (int st = committed + 1; st < issued; ++st)
+            mbar_wait(full0 + 8 * (st % NB), (uint32_t)((st / NB) & 1));
+        if (committed >= 0)
+            mbar_wait(empty0 + 8 * (committed % NB), (uint32_t)((committed / NB) & 1));
+    }
     __syncthreads();
-    // on a failed wait, give the last committed MMAs (bounded) time to land
-    // before their TMEM is freed
-    if (!ok && last >= 0) mbar_wait(mbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1));
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
@@ -299,17 +314,59 @@ k_oz_umma(int m, int n, int64_t kpad, int64_t kc, const uint16_t* __restrict__ A
     }
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+    static std::once_flag once;
+    static EncodeFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// the slices of an operand as a 3-d tensor (k, row, batch x slice) of
+// 16-bit elements; boxes of 64 k x box_rows rows, 128-byte swizzle
+cudaError_t slice_map(CUtensorMap* map, const OzOperand& op, int nb, int box_rows) {
+    EncodeFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)op.kpad, (cuuint64_t)op.rows_pad,
+                                (cuuint64_t)nb * (cuuint64_t)op.S};
+    const cuuint64_t strides[2] = {(cuuint64_t)op.kpad * 2,
+                                   (cuuint64_t)op.rows_pad * (cuuint64_t)op.kpad * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, op.slices, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int S>
 cudaError_t umma_gemm_t(int nb, int m, int n, int64_t kpad, int nsplit, const OzOperand& A,
                         const OzOperand& B, double alpha, double beta, double* C, int64_t ldc,
                         int64_t strideC, int64_t strideSplit, int sym, int* err, cudaStream_t s) {
     constexpr int smem = TcSmem<S>::BYTES;
+    CUtensorMap ta, tb;
+    RK_CUDA_TRY(slice_map(&ta, A, nb, TBM));
+    RK_CUDA_TRY(slice_map(&tb, B, nb, TBN));
     RK_CUDA_TRY(cudaFuncSetAttribute(k_oz_umma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const int64_t kc = round_up(ceil_div(kpad, nsplit), 32);
+    // split chunks on stage boundaries: a tensor copy past a chunk's end would
+    // read the next chunk (past kpad it reads zeros)
+    const int64_t kc = round_up(ceil_div(kpad, nsplit), TBK);
     dim3 grid((unsigned)ceil_div(n, TBN), (unsigned)ceil_div(m, TBM), (unsigned)(nb * nsplit));
-    k_oz_umma<S><<<grid, 128, smem, s>>>(m, n, kpad, kc, A.slices, A.amax, A.rows_pad, B.slices,
-                                         B.amax, B.rows_pad, alpha, beta, C, ldc, strideC,
-                                         strideSplit, nsplit, sym, err);
+    k_oz_umma<S><<<grid, 128, smem, s>>>(ta, tb, m, n, kpad, kc, A.amax, A.rows_pad, B.amax,
+                                         B.rows_pad, alpha, beta, C, ldc, strideC, strideSplit,
+                                         nsplit, sym, err);
     return cudaGetLastError();
 }
 

@@ -378,8 +378,13 @@ void scheduler(svd_server_s* s) {
             for (size_t i = 0; i < admitted.size(); ++i) {
                 std::vector<Request*> run;
                 const int slot = admitted[i][0]->slot;
+                // a failed request's plan must leave the batch before it is freed.
+                // The slot's stream was synchronised above whenever a member
+                // failed, so the batched pass of the survivors has finished
+                // (batch_engine_detach's precondition); their completion only
+                // waits on the group's event and frees them afterwards.
                 for (size_t j = 0; j < admitted[i].size(); ++j)
-                    if (res[i][j] != SVD_OK) {   // a failed request's plan must leave the batch
+                    if (res[i][j] != SVD_OK) {
                         batch_engine_detach(s->engines[slot]);
                         break;
                     }
