@@ -123,6 +123,12 @@ typedef struct {
                                         ranks <= D M) less device memory.
                                         Rejected by svd_batch_create and run alone
                                         by the server. */
+    int32_t jacobi_cluster;          /* mixed precision: CTAs (thread-block cluster
+                                        size 1, 2, 4, 8 or 16) per block matrix in
+                                        the FP32 Jacobi launch; 0 = chosen from the
+                                        occupancy model (the autotuner sets it from
+                                        measurements); a size that cannot be
+                                        launched falls back to 0 */
     int32_t merge_rank;              /* k' > 0: every block (and tree node) passes at
                                         most its k' largest singular directions
                                         upward (the approximate truncation of the
@@ -145,10 +151,6 @@ typedef struct {
                                  warp-level mma.sync tensor path instead of tcgen05.mma
                                  with TMEM accumulators (bit-identical results; for
                                  testing and timing) */
-#define SVD_FLAG_ATOMIC_GRAM 128 /* form the block cross products with global FP64 atomics
-                                 (plus separate mirror and conversion passes) instead of
-                                 the thread-block-cluster form (same values up to the
-                                 summation order; for testing and timing) */
 #define SVD_FLAG_TALL 32       /* tall-and-skinny A: M rows (any, >= 1) and N <= 1024
                                  columns, split into num_blocks ROW blocks (the row-block
                                  form of section II); block_col_bounds then holds D+1

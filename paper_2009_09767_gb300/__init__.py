@@ -37,7 +37,6 @@ FLAG_DENSE_REFINE = 8
 FLAG_FP64_PRODUCTS = 16
 FLAG_TALL = 32
 FLAG_LEGACY_MMA = 64
-FLAG_ATOMIC_GRAM = 128
 STAGES = ["partition", "gram", "block_jacobi", "block_refine", "sort_proxy", "merge_gram",
           "merge_eig", "finalize", "spmm"]
 
@@ -62,7 +61,8 @@ class SvdDesc(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("rank_tol", ctypes.c_double),
         ("max_sweeps", ctypes.c_int32), ("jacobi_tol", ctypes.c_double),
         ("refine_iters", ctypes.c_int32), ("flags", ctypes.c_int32),
-        ("merge_arity", ctypes.c_int32), ("merge_rank", ctypes.c_int32),
+        ("merge_arity", ctypes.c_int32), ("jacobi_cluster", ctypes.c_int32),
+        ("merge_rank", ctypes.c_int32),
     ]
 
 
@@ -112,7 +112,8 @@ def _check(status: int, what: str):
 
 def make_desc(M, N, nnz, num_blocks, *, bounds=None, k=0, precision="mixed",
               rank_fix="truncate", seed=0, value_type="f32", rank_tol=0.0, max_sweeps=0,
-              jacobi_tol=0.0, refine_iters=-1, flags=0, merge_arity=0, merge_rank=0):
+              jacobi_tol=0.0, refine_iters=-1, flags=0, merge_arity=0, merge_rank=0,
+              jacobi_cluster=0):
     d = SvdDesc()
     d.M, d.N, d.nnz = int(M), int(N), int(nnz)
     d.value_type = VALUE[value_type] if isinstance(value_type, str) else int(value_type)
@@ -132,6 +133,7 @@ def make_desc(M, N, nnz, num_blocks, *, bounds=None, k=0, precision="mixed",
     d.flags = int(flags)
     d.merge_arity = int(merge_arity)
     d.merge_rank = int(merge_rank)
+    d.jacobi_cluster = int(jacobi_cluster)
     return d, keep
 
 

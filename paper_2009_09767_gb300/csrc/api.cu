@@ -453,31 +453,18 @@ svd_status phase_pre(svd_plan_s* p, const RunIO& io, cudaStream_t s) {
                                              p->patch_ofs, ext, io.npatches, s));
     }
     mark(p, 1, s);
-    // without insertions: the cluster form writes the full matrices and the
-    // solver's copy in one pass; with insertions (added by atomics to the
-    // upper triangle), or where clusters cannot run, the atomic form
-    bool done = false;
-    if (!p->patched && !(p->d.flags & SVD_FLAG_ATOMIC_GRAM)) {
-        CU(launch_gram_cluster(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->bounds_d, p->G64,
-                               p->mixed ? p->G32 : nullptr, p->mixed ? nullptr : p->Gw64, s, &done));
-        if (done) ++p->launches;
-    }
-    if (!done) {
-        CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
-        LAUNCH(p, 1, launch_gram(io.col_ptr, io.row_idx, io.vals, vt, Mp, p->nchunks, p->chunk_block,
-                                 p->chunk_lo, p->chunk_hi, p->G64, s));
-        if (p->patched)
-            LAUNCH(p, 1, launch_gram_patches(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->patches,
-                                             p->patch_ofs, D * M, p->G64, s));
-        LAUNCH(p, 1, launch_symmetrize(p->G64, D, Mp, s));
-    }
+    CU(cudaMemsetAsync(p->G64, 0, sizeof(double) * (size_t)D * mm, s));
+    LAUNCH(p, 1, launch_gram(io.col_ptr, io.row_idx, io.vals, vt, Mp, p->nchunks, p->chunk_block,
+                             p->chunk_lo, p->chunk_hi, p->G64, s));
+    if (p->patched)
+        LAUNCH(p, 1, launch_gram_patches(io.col_ptr, io.row_idx, io.vals, vt, Mp, D, p->patches,
+                                         p->patch_ofs, D * M, p->G64, s));
+    LAUNCH(p, 1, launch_symmetrize(p->G64, D, Mp, s));
     mark(p, 2, s);
-    if (!done) {
-        if (!p->mixed)
-            CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * D * mm, cudaMemcpyDeviceToDevice, s));
-        else
-            LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, (int64_t)D * mm, s));
-    }
+    if (!p->mixed)
+        CU(cudaMemcpyAsync(p->Gw64, p->G64, sizeof(double) * D * mm, cudaMemcpyDeviceToDevice, s));
+    else
+        LAUNCH(p, 1, launch_convert_f64_f32(p->G64, p->G32, (int64_t)D * mm, s));
     return SVD_OK;
 }
 
@@ -487,7 +474,7 @@ svd_status block_jacobi(svd_plan_s* p, cudaStream_t s) {
                                            p->jac_tol, p->sweeps, s));
     else
         LAUNCH(p, 1, launch_jacobi<float>(p->G32, p->Vt32, p->D, p->Mp, p->max_sweeps, p->jac_tol,
-                                          p->sweeps, s, p->jwork));
+                                          p->sweeps, s, p->jwork, p->d.jacobi_cluster));
     return SVD_OK;
 }
 

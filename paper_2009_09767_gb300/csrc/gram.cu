@@ -7,8 +7,6 @@
 // One CTA streams a column chunk (all in one block) and scatters the
 // upper-triangle products of its columns with FP64 atomic adds into the
 // block's M x M matrix (row-major, padded to Mp).
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "common.cuh"
@@ -70,167 +68,6 @@ k_gram(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
             }
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// Cluster form: one thread-block cluster per block (and pass) keeps the
-// packed upper triangle of that block's cross product in the distributed
-// shared memory of its CTAs (element (r1 <= r2) at r1 Mp - r1 (r1 - 1) / 2 +
-// r2 - r1, CTA idx / per_cta owns it), every CTA scatters the products of
-// its share of the block's columns into it with shared-memory atomics
-// (local or on a peer CTA), and after a cluster barrier each CTA writes its
-// rows of the full symmetric matrix once, coalesced, in FP64 and in the
-// solver's type.  Blocks whose triangle exceeds the cluster's shared memory
-// take several passes, each owning a range of the packed indices.
-namespace {
-__device__ __forceinline__ int packed_index(int r1, int r2, int Mp) {
-    return r1 * Mp - (r1 * (r1 - 1)) / 2 + (r2 - r1);
-}
-
-template <typename T2>
-__global__ void __launch_bounds__(kThreads)
-k_gram_cluster(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-               const void* __restrict__ vals, int value_type, int Mp,
-               const int64_t* __restrict__ bounds, int npass, int per_cta, double* __restrict__ G,
-               T2* __restrict__ G2) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int CS = (int)cluster.num_blocks();
-    const int crank = (int)cluster.block_rank();
-    const int cl = blockIdx.x / CS;
-    const int d = cl / npass, pass = cl % npass;
-    extern __shared__ double tri[];                 // per_cta packed elements
-    const int base = pass * CS * per_cta;           // first packed index of this pass
-    const int total = Mp * (Mp + 1) / 2;
-    for (int e = threadIdx.x; e < per_cta; e += kThreads) tri[e] = 0.0;
-    cluster.sync();
-    const int64_t lo = bounds[d], hi = bounds[d + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kWarps = kThreads / 32;
-    __shared__ int64_t heavy[kThreads * 4];
-    __shared__ int nheavy;
-    auto add = [&](int r1, int r2, double v) {
-        const int idx = packed_index(r1, r2, Mp) - base;
-        if (idx < 0 || idx >= CS * per_cta) return;
-        const int owner = idx / per_cta;
-        double* t = cluster.map_shared_rank(tri, owner);
-        atomicAdd(t + (idx - owner * per_cta), v);
-    };
-    // the CTA's columns: lo + crank, lo + crank + CS, ...; light ones by a
-    // thread, long ones queued for a warp (in rounds that fit the queue)
-    for (int64_t j0 = lo + crank; j0 < hi; j0 += (int64_t)CS * kThreads * 8) {
-        if (threadIdx.x == 0) nheavy = 0;
-        __syncthreads();
-        const int64_t j1 = min(hi, j0 + (int64_t)CS * kThreads * 8);
-        for (int64_t j = j0 + (int64_t)threadIdx.x * CS; j < j1; j += (int64_t)CS * kThreads) {
-            const int64_t e0 = col_ptr[j], e1 = col_ptr[j + 1];
-            if (e1 - e0 > kLight) {
-                const int h = atomicAdd(&nheavy, 1);
-                if (h < kThreads * 4) { heavy[h] = j; continue; }
-            }
-            for (int64_t a = e0; a < e1; ++a) {
-                const double va = load_val(vals, value_type, a);
-                if (va == 0.0) continue;
-                const int ra = row_idx[a];
-                for (int64_t b = a; b < e1; ++b) {
-                    const double vb = load_val(vals, value_type, b);
-                    if (vb != 0.0) add(ra, row_idx[b], va * vb);
-                }
-            }
-        }
-        __syncthreads();
-        const int nh = min(nheavy, kThreads * 4);
-        for (int h = warp; h < nh; h += kWarps) {
-            const int64_t j = heavy[h];
-            const int64_t e0 = col_ptr[j], e1 = col_ptr[j + 1];
-            for (int64_t a = e0; a < e1; ++a) {
-                const double va = load_val(vals, value_type, a);
-                if (va == 0.0) continue;
-                const int ra = row_idx[a];
-                for (int64_t b = a + lane; b < e1; b += 32) {
-                    const double vb = load_val(vals, value_type, b);
-                    if (vb != 0.0) add(ra, row_idx[b], va * vb);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    cluster.sync();
-    // rows of the full matrix: this CTA writes the elements whose packed
-    // index (of the upper-triangle position) falls in this pass, rows
-    // crank, crank + CS, ... (row r: one coalesced pass over its Mp entries)
-    const int64_t mm = (int64_t)Mp * Mp;
-    double* Gd = G + (int64_t)d * mm;
-    T2* G2d = G2 ? G2 + (int64_t)d * mm : nullptr;
-    for (int r = crank; r < Mp; r += CS) {
-        for (int c = threadIdx.x; c < Mp; c += kThreads) {
-            const int r1 = min(r, c), r2 = max(r, c);
-            const int idx = packed_index(r1, r2, Mp) - base;
-            if (idx < 0 || idx >= CS * per_cta || idx + base >= total) continue;
-            const int owner = idx / per_cta;
-            const double v = *(cluster.map_shared_rank(tri, owner) + (idx - owner * per_cta));
-            Gd[(int64_t)r * Mp + c] = v;
-            if (G2d) G2d[(int64_t)r * Mp + c] = (T2)v;
-        }
-    }
-    // no CTA leaves while peers read its shared memory
-    cluster.sync();
-}
-
-template <typename T2>
-cudaError_t gram_cluster_t(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
-                           int value_type, int Mp, int D, const int64_t* bounds, double* G, T2* G2,
-                           cudaStream_t s, bool* done) {
-    *done = false;
-    auto kern = k_gram_cluster<T2>;
-    int CS = 16;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        CS = 8;
-    }
-    // shared memory per CTA at most ~100 KB (two CTAs per SM); passes split
-    // the packed triangle
-    const int64_t total = (int64_t)Mp * (Mp + 1) / 2;
-    constexpr int64_t kMaxPerCta = (100 * 1024) / 8;
-    const int npass = (int)ceil_div(total, (int64_t)CS * kMaxPerCta);
-    const int per_cta = (int)ceil_div(total, (int64_t)CS * npass);
-    const size_t smem = sizeof(double) * (size_t)per_cta;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return cudaSuccess;   // not done: the caller takes the atomic form
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(D * npass * CS), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
-        cudaGetLastError();
-        return cudaSuccess;
-    }
-    RK_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, col_ptr, row_idx, vals, value_type, Mp, bounds, npass,
-                                   per_cta, G, G2));
-    *done = true;
-    return cudaSuccess;
-}
-}  // namespace
-
-cudaError_t launch_gram_cluster(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
-                                int value_type, int Mp, int D, const int64_t* bounds, double* G,
-                                float* G32, double* G64copy, cudaStream_t s, bool* done) {
-    if (G64copy)
-        return gram_cluster_t<double>(col_ptr, row_idx, vals, value_type, Mp, D, bounds, G, G64copy,
-                                      s, done);
-    return gram_cluster_t<float>(col_ptr, row_idx, vals, value_type, Mp, D, bounds, G, G32, s, done);
 }
 
 cudaError_t launch_gram(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,

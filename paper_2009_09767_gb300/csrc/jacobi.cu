@@ -1097,6 +1097,37 @@ k_jacobi4_items(const JacobiItem* __restrict__ items, int nitems, int* __restric
 // maximum active clusters.
 constexpr int kSolve4 = 4;
 
+// Whether a cluster of cs CTAs of the FP32 solver can be resident.
+bool cluster_fits4(int cs) {
+    if (cs > 8 && cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)J4Smem::bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs, 1, 1);
+    cfg.blockDim = dim3(kJT4, 1, 1);
+    cfg.dynamicSmemBytes = J4Smem::bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi4, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 int pick_cluster4(int nmat, int Mp) {
     const int np = Mp / kB2;
     const int64_t jobs = (int64_t)np * (np + 1) / 2 + (int64_t)np * (Mp / kB2);
@@ -1201,13 +1232,19 @@ size_t jacobi_work_bytes(int nmat, int Mp) {
 
 template <typename T>
 cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
-                          int32_t* sweeps, cudaStream_t s, void* work) {
+                          int32_t* sweeps, cudaStream_t s, void* work, int cluster) {
     if (nmat <= 0) return cudaSuccess;
     if (Mp % kB2 != 0) return cudaErrorInvalidValue;
     const int npairs = Mp / kB2;
     if constexpr (sizeof(T) == 4) {
         if (!work) return cudaErrorInvalidValue;
-        const int csize = pick_cluster4(nmat, Mp);
+        // a requested cluster size (1, 2, 4, 8 or 16) that cannot be launched
+        // falls back to the occupancy model's choice
+        int csize = -1;
+        if (cluster >= 1 && cluster <= kMaxCluster && (cluster & (cluster - 1)) == 0 &&
+            cluster_fits4(cluster))
+            csize = cluster;
+        if (csize < 1) csize = pick_cluster4(nmat, Mp);
         if (csize < 1) return cudaErrorInvalidConfiguration;
         if (csize > 8)
             RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -1284,9 +1321,9 @@ cudaError_t launch_jacobi_items(const JacobiItem* items, int nitems, int max_mp,
 }
 
 template cudaError_t launch_jacobi<float>(float*, float*, int, int, int, double, int32_t*,
-                                          cudaStream_t, void*);
+                                          cudaStream_t, void*, int);
 template cudaError_t launch_jacobi<double>(double*, double*, int, int, int, double, int32_t*,
-                                           cudaStream_t, void*);
+                                           cudaStream_t, void*, int);
 template cudaError_t launch_jacobi_items<float>(const JacobiItem*, int, int, int*, int, double,
                                                 cudaStream_t);
 template cudaError_t launch_jacobi_items<double>(const JacobiItem*, int, int, int*, int, double,

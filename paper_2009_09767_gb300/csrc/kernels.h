@@ -47,15 +47,6 @@ cudaError_t launch_gram(const int64_t* col_ptr, const int32_t* row_idx, const vo
 cudaError_t launch_gram_patches(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
                                 int value_type, int Mp, int D, const PatchRec* patches,
                                 const int64_t* patch_ofs, int max_patches, double* G, cudaStream_t s);
-// The same cross products formed in thread-block clusters (distributed shared
-// memory, one cluster per block and pass), written once as full symmetric
-// matrices G, and also converted into G32 (when G32 is given) or copied into
-// G64copy (when given); G needs no clearing.  bounds: D+1 column bounds on
-// the device.  *done = false when this device cannot run the cluster form
-// (nothing was enqueued; use launch_gram instead).
-cudaError_t launch_gram_cluster(const int64_t* col_ptr, const int32_t* row_idx, const void* vals,
-                                int value_type, int Mp, int D, const int64_t* bounds, double* G,
-                                float* G32, double* G64copy, cudaStream_t s, bool* done);
 // Mirror the upper triangle into the lower one, in place, for nmat matrices.
 cudaError_t launch_symmetrize(double* G, int nmat, int Mp, cudaStream_t s);
 cudaError_t launch_convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
@@ -67,9 +58,10 @@ cudaError_t launch_convert_f32_f64(const float* src, double* dst, int64_t n, cud
 // sweep count, negative when max_sweeps ran out.  The FP32 solver needs
 // work = jacobi_work_bytes(nmat, Mp) bytes of device memory (the published
 // pair rotations); the FP64 one ignores it.
+// cluster (FP32 solver): CTAs per matrix, 0 = the occupancy model's choice.
 template <typename T>
 cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double tol,
-                          int32_t* sweeps, cudaStream_t s, void* work = nullptr);
+                          int32_t* sweeps, cudaStream_t s, void* work = nullptr, int cluster = 0);
 size_t jacobi_work_bytes(int nmat, int Mp);
 // Padded order of an M x M problem (a multiple of 32).
 int jacobi_pad(int M);

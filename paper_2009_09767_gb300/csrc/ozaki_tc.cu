@@ -15,10 +15,11 @@
 // CTA: 128 threads, output tile 128 x 32 (row i of the tile = TMEM lane i =
 // thread i at the drain), S (S + 1) / 2 <= 15 accumulators of 32 columns in
 // one 512-column TMEM allocation.  k runs in stages of 64 through NBUF shared
-// buffers; one thread issues each stage's tensor copies (one per slice and
-// operand, completion counted in bytes on the buffer's "full" mbarrier) and,
-// once they have landed, the stage's MMAs (M = 128, N = 32, K = 16), which it
-// commits to the buffer's "empty" mbarrier before refilling the buffer.
+// buffers.  Warp 0 runs the pipeline (lane 0 issues): each stage's tensor
+// copies (one per slice and operand, completion counted in bytes on the
+// buffer's "full" mbarrier) and, once they have landed, the stage's MMAs
+// (M = 128, N = 32, K = 16), committed to the buffer's "empty" mbarrier
+// before the buffer is refilled; the other warps wait for the drain.
 // Shared tiles are K-major with the 128-byte swizzle: rows of 64 bf16, 8-row
 // atoms of 1024 bytes; along k inside an atom the descriptor start advances
 // by 32 bytes per MMA.  Every wait is bounded: on expiry the CTA records an
@@ -219,41 +220,62 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     };
 
     int period = 0;
+    const int lane = tid & 31;
     for (int p0 = 0; p0 < nst; p0 += kStagesPerDrain, ++period) {
         const int p1 = min(nst, p0 + kStagesPerDrain);
-        if (tid == 0 && !failed) {
-            for (int st = p0; st < min(p1, p0 + NB); ++st) issue_loads(st);
+        // warp 0 runs the copy/MMA loop with uniform control flow (every lane
+        // waits, lane 0 issues); warps 1..3 go straight to the drain wait
+        if (warp == 0 && !failed) {
+            if (lane == 0)
+                for (int st = p0; st < min(p1, p0 + NB); ++st) issue_loads(st);
             issued = min(p1, p0 + NB);
+            bool ok = true;
             for (int it = p0; it < p1; ++it) {
                 const int buf = it % NB;
                 const uint32_t par = (uint32_t)((it / NB) & 1);
-                if (!mbar_wait(full0 + 8 * buf, par)) { failed = 1; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sb = sbase + buf * L::STAGE;
-                int p = 0;
-#pragma unroll 1
-                for (int a = 1; a <= S; ++a) {
-#pragma unroll 1
-                    for (int bs = 1; a + bs <= S + 1; ++bs, ++p) {
-                        const uint32_t sa = sb + (a - 1) * L::A_BYTES;
-                        const uint32_t sbb = sb + S * L::A_BYTES + (bs - 1) * L::B_BYTES;
+                ok = __all_sync(0xffffffffu, mbar_wait(full0 + 8 * buf, par));
+                if (!ok) break;
+                if (lane == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sb = sbase + buf * L::STAGE;
+                    // descriptors of slice 1 at k = 0; a slice and a 16-k step move
+                    // only the start-address field (16-byte units, no carry:
+                    // shared addresses stay below 2^18)
+                    const uint64_t dA = umma_desc_sw128(sb);
+                    const uint64_t dB = umma_desc_sw128(sb + S * L::A_BYTES);
+                    const uint32_t first = it == p0 ? 0u : 1u;
 #pragma unroll
-                        for (int kk = 0; kk < TBK / 16; ++kk)
-                            umma_bf16(tbase + (uint32_t)(p * TBN), umma_desc_sw128(sa + kk * 32),
-                                      umma_desc_sw128(sbb + kk * 32),
-                                      (it == p0 && kk == 0) ? 0u : 1u);
+                    for (int a = 1; a <= S; ++a) {
+#pragma unroll
+                        for (int bs = 1; a + bs <= S + 1; ++bs) {
+                            const int p = (a - 1) * (2 * S + 2 - a) / 2 + (bs - 1);
+#pragma unroll
+                            for (int kk = 0; kk < TBK / 16; ++kk)
+                                umma_bf16(tbase + (uint32_t)(p * TBN),
+                                          dA + (uint64_t)(((a - 1) * L::A_BYTES + kk * 32) >> 4),
+                                          dB + (uint64_t)(((bs - 1) * L::B_BYTES + kk * 32) >> 4),
+                                          kk == 0 ? first : 1u);
+                        }
                     }
+                    umma_commit(empty0 + 8 * buf);
                 }
-                umma_commit(empty0 + 8 * buf);
+                __syncwarp();
                 committed = it;
                 if (it + NB < p1) {
                     // the buffer is refilled once the MMAs reading it are done
-                    if (!mbar_wait(empty0 + 8 * buf, par)) { failed = 1; break; }
-                    issue_loads(it + NB);
+                    ok = __all_sync(0xffffffffu, mbar_wait(empty0 + 8 * buf, par));
+                    if (!ok) break;
+                    if (lane == 0) issue_loads(it + NB);
+                    __syncwarp();
                     issued = it + NB + 1;
                 }
             }
-            if (!failed) umma_commit(drainb);
+            if (!ok) {
+                if (lane == 0) failed = 1;
+            } else if (lane == 0) {
+                umma_commit(drainb);
+            }
+            __syncwarp();
         }
         // drain: every thread, once the period's MMAs are done
         if (!mbar_wait(drainb, (uint32_t)(period & 1), &failed)) failed = 1;
@@ -279,7 +301,7 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         __syncthreads();
     }
     const bool ok = !failed;
-    if (!ok && tid == 0) {
+    if (!ok && tid == 0) {   // (issued and committed are warp 0's, uniform across it)
         // let what was issued land before the shared memory and TMEM go away
         for (int st = committed + 1; st < issued; ++st)
             mbar_wait(full0 + 8 * (st % NB), (uint32_t)((st / NB) & 1));

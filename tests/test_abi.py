@@ -51,7 +51,7 @@ def test_struct_layout_matches_c(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",
     sizeof(svd_desc), offsetof(svd_desc, N), offsetof(svd_desc, nnz),
     offsetof(svd_desc, value_type), offsetof(svd_desc, num_blocks),
     offsetof(svd_desc, block_col_bounds), offsetof(svd_desc, k),
@@ -59,7 +59,7 @@ int main(void) {{
     offsetof(svd_desc, rank_tol), offsetof(svd_desc, max_sweeps),
     offsetof(svd_desc, jacobi_tol), offsetof(svd_desc, refine_iters),
     offsetof(svd_desc, flags), offsetof(svd_desc, merge_arity),
-    offsetof(svd_desc, merge_rank), sizeof(svd_patch));
+    offsetof(svd_desc, jacobi_cluster), offsetof(svd_desc, merge_rank), sizeof(svd_patch));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -70,7 +70,8 @@ int main(void) {{
               D.num_blocks.offset, D.block_col_bounds.offset, D.k.offset, D.precision.offset,
               D.rank_fix.offset, D.seed.offset, D.rank_tol.offset, D.max_sweeps.offset,
               D.jacobi_tol.offset, D.refine_iters.offset, D.flags.offset,
-              D.merge_arity.offset, D.merge_rank.offset, ctypes.sizeof(rk.SvdPatch)]
+              D.merge_arity.offset, D.jacobi_cluster.offset, D.merge_rank.offset,
+              ctypes.sizeof(rk.SvdPatch)]
     assert got == expect
 
 
