@@ -555,6 +555,8 @@ def main():
                     help="zipf_wide: serving sweep as precision:rate pairs")
     ap.add_argument("--serve-duration", type=float, default=2.0)
     ap.add_argument("--serve-grace", type=float, default=2.0)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="zipf_wide: skip the Jacobi launch-shape autotuner")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -589,8 +591,16 @@ def main():
     cp = torch.from_numpy(case.col_ptr).to(dev)
     ri = torch.from_numpy(case.row_idx).to(dev)
     va = torch.from_numpy(case.vals).to(dev)
+    # launch shape of the FP32 Jacobi (CTAs per block matrix), measured
+    tuned = None
+    if args.precision == "mixed" and not args.no_tune:
+        from paper_2009_09767_gb300 import autotune
+        cs, cs_ms = autotune.tune_cluster(case, device=dev)
+        tuned = {"jacobi_cluster": cs, "block_jacobi_ms_by_cluster": cs_ms,
+                 "note": "0 = the library's occupancy model"}
     plan = rk.Plan(case.M, case.N, case.nnz, case.num_blocks, value_type=vt,
-                   precision=args.precision, flags=rk.FLAG_TIMING)
+                   precision=args.precision, flags=rk.FLAG_TIMING,
+                   jacobi_cluster=tuned["jacobi_cluster"] if tuned else 0)
     out = rk.alloc_outputs(plan, device=dev, with_patches=False)
     stream = torch.cuda.current_stream(dev)
 
@@ -762,7 +772,7 @@ def main():
                        "l2": "no flush: each step writes V (N x k, >= 2 GB) and a >= 0.5 GB "
                              "workspace, far above the 129 MB L2"},
             "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
-            "plain_fp64": plain, "serving": serving,
+            "plain_fp64": plain, "serving": serving, "autotune": tuned,
             "gpu_launches": launches * args.steps, "launches_per_step": launches,
             "clocks": clock_info, "stage_ms": stage_ms, "hbm_kernels": hbm_kernels,
             "sweeps": {"blocks_min": int(np.abs(sweeps[:-1]).min()),

@@ -100,3 +100,35 @@ def tune(cases, precision: str = "mixed", sample: int = 64, reps: int = 2, devic
         except OSError:
             pass
     return width, rates
+
+
+# FP32 Jacobi launch shape: CTAs per block matrix (thread-block cluster size).
+CLUSTER_CANDIDATES = (0, 2, 4, 8, 16)   # 0: the library's occupancy model
+
+
+def tune_cluster(case, precision: str = "mixed", reps: int = 2, device=None, candidates=None):
+    """Measure the block-eigensolve stage (SVD_FLAG_TIMING stage times) of
+    one matrix for each Jacobi cluster size; return (best size, {size: ms}).
+    The size only changes how the solver is spread over the GPU, never the
+    result beyond rounding."""
+    import torch
+
+    import paper_2009_09767_gb300 as rk
+    device = device or torch.device("cuda")
+    cp, ri, va = (torch.from_numpy(a).to(device) for a in (case.col_ptr, case.row_idx, case.vals))
+    times = {}
+    for cs in candidates or CLUSTER_CANDIDATES:
+        p = rk.Plan(case.M, case.N, case.nnz, case.num_blocks, value_type="f32",
+                    precision=precision, flags=rk.FLAG_TIMING | rk.FLAG_SKIP_V, jacobi_cluster=cs)
+        o = rk.alloc_outputs(p, device=device, with_patches=False)
+        p.run(cp, ri, va, o["sigma"], o["U"], None, o["rank"])
+        p.sync()
+        p.query(rk.Q_STAGE_TOTAL)   # reset the stage sums
+        for _ in range(reps):
+            p.run(cp, ri, va, o["sigma"], o["U"], None, o["rank"])
+        p.sync()
+        tot = p.query(rk.Q_STAGE_TOTAL)
+        times[str(cs)] = float(tot[rk.STAGES.index("block_jacobi")] / max(tot[-1], 1))
+        p.free()
+    best = min(times, key=times.get)
+    return int(best), times

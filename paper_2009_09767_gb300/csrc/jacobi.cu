@@ -758,7 +758,7 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
 
 template <int K>
 __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp, int* rq, int* act,
-                            float tol, float floor_abs, int& rotated, int wi, int bar) {
+                            float tol, float floor_abs, int& rotated, int wi, int bar, bool cross) {
     constexpr int LD = J4Smem::LD;
     constexpr int NU = kB / K;                 // pairs per warp per pass
     constexpr int HB = NU > 8 ? 8 : NU;        // pairs held in registers at once
@@ -767,7 +767,11 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
     float fa = 0.f, fd = 0.f;
     int fp = -1, fq = 0;
     bool any_round = false;
-    for (int r = 0; r < kB2 - 1; ++r) {
+    // all 496 pairs of the sub-problem in 31 rounds, or (cross) only the 256
+    // pairs between its two index blocks in 16 rounds: pair u of round r is
+    // (u, 16 + (u + r) mod 16)
+    const int rounds = cross ? kB : kB2 - 1;
+    for (int r = 0; r < rounds; ++r) {
         if (wi == 0) {
             if (fp >= 0) {
                 sub[fp * LD + fp] = fa;
@@ -778,7 +782,12 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
             __syncwarp();
             if (lane < kB) {
                 int p, q;
-                circle_pair(kB2, r, lane, p, q);
+                if (cross) {
+                    p = lane;
+                    q = kB + ((lane + r) & (kB - 1));
+                } else {
+                    circle_pair(kB2, r, lane, p, q);
+                }
                 const float a = sub[p * LD + p], d = sub[q * LD + q], g = sub[p * LD + q];
                 float c = 1.f, sn = 0.f;
                 fp = -1;
@@ -870,7 +879,11 @@ __device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step
         Q[i * LD + lane] = i == lane ? 1.f : 0.f;
     }
     group_bar(bar, 32 * K);
-    const bool moved = group_sweep<K>(sub, Q, rc, rs, rp, rq, act, tol, floor_abs, rotated, wi, bar);
+    // the pairs inside each index block are taken at the sweep's first step
+    // (every block takes part in it), the pairs between the two blocks at
+    // every step: each pair once per sweep at least
+    const bool moved = group_sweep<K>(sub, Q, rc, rs, rp, rq, act, tol, floor_abs, rotated, wi, bar,
+                                      step != 0);
     if (wi == 0 && (threadIdx.x & 31) == 0) ident[u] = moved ? 0 : 1;
     uint32_t* qo = qbuf + (size_t)u * 2 * kQWords;
     for (int w = wi; w < kB; w += K) {
