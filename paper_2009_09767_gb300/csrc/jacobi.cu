@@ -533,11 +533,21 @@ constexpr int kQWords = kB2 * kB2 / 2;         // 32-bit words of one 32 x 32 f1
 constexpr float kQScale = 16384.f;             // 2^14: Q and V as split operands
 constexpr float kQInv = 1.f / 16384.f;
 
+// Update jobs may stage their global operand (32 rows x the 32 columns of
+// P_u) in a per-warp shared buffer with cp.async: the next job's copy is
+// in flight while the current job computes.  Rows are padded to 40 floats,
+// so that the 8-byte fragment loads of a half warp hit 32 distinct banks.
+constexpr int kStageLD = 40;
+constexpr size_t kStageBytes = (size_t)kB2 * kStageLD * sizeof(float);
+
 struct J4Smem {
     static constexpr int LD = kB2 + 1;
     // per warp: sub-problem, its rotation, the round's rotation table
-    static constexpr size_t per_warp = sizeof(float) * (2 * kB2 * LD + 2 * kB) + sizeof(int) * (2 * kB + 4);
-    static constexpr size_t bytes = per_warp * kW4;
+    // (c, s, p, q per pair as one float4) and the round flags
+    static constexpr size_t per_warp = sizeof(float) * 2 * kB2 * LD + sizeof(float4) * kB + sizeof(int) * 4;
+    static constexpr size_t solve_bytes = per_warp * kW4;
+    static constexpr size_t staged_bytes = solve_bytes + kW4 * kStageBytes;
+    static constexpr size_t bytes(bool staged) { return staged ? staged_bytes : solve_bytes; }
 };
 
 // 32-bit words of solver work per matrix: np published rotations (2 kQWords
@@ -570,14 +580,69 @@ __device__ __forceinline__ void mma_split(float (&d)[4], const uint32_t (&ah)[4]
     mma_f16(d, ah, bh0, bh1);
 }
 
-// rotation words from the CTA's shared copy (kS) or from L2
-template <bool kS>
-__device__ __forceinline__ uint32_t ldq(const uint32_t* p) {
-    if constexpr (kS) return *p;
-    else return __ldcg(p);
+// Rotation word off of a published (2^14 Q)^T from the CTA's shared copy
+// (kS) or from L2.  The staged kernels store their shared copy with the
+// 16-byte groups of each 16-word row XOR-ed by (row / 2) mod 4, so that the
+// eight rows one fragment load touches fall in distinct banks (kSw).
+template <bool kS, bool kSw>
+__device__ __forceinline__ uint32_t ldq(const uint32_t* q, int off) {
+    if constexpr (kS && kSw) return q[off ^ (((off >> 5) & 3) << 2)];
+    else if constexpr (kS) return q[off];
+    else return __ldcg(q + off);
 }
 __device__ __forceinline__ float2 ldcg_f2(const float* p) {
     return __ldcg(reinterpret_cast<const float2*>(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Stage rows row(n), n < 32, of Mat at the 32 columns of P_u = (ui, uj) into
+// stg[n][k]: row(n) = P_w(n) of a block job (blk), r0 + n of a column job.
+// Each 16-byte copy stays inside one 16-column half of P_u.
+__device__ __forceinline__ void stage_rows(float* stg, const float* Mat, int Mp, int ui, int uj, bool blk,
+                                           int wi, int wj, int r0) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = i * 32 + lane;
+        const int n = c >> 3, k = (c & 7) * 4;
+        const int row = blk ? gidx(wi, wj, n) : r0 + n;
+        cp_async16(stg + n * kStageLD + k, Mat + (int64_t)row * Mp + gidx(ui, uj, k));
+    }
+    cp_async_commit();
+}
+
+// Fragments of a staged block job (B[k][n] = stg[n][k]) and of a staged
+// column job (A[m][k] = stg[m][k]) in the order job_block / job_vcols take.
+__device__ __forceinline__ void frag_block(const float* stg, float2 (&op)[16]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                op[(kk * 4 + nj) * 2 + h] =
+                    *reinterpret_cast<const float2*>(stg + (nj * 8 + g) * kStageLD + kk * 16 + 2 * t + 8 * h);
+}
+__device__ __forceinline__ void frag_vcols(const float* stg, float2 (&op)[16]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const float* r = stg + (mi * 16 + g) * kStageLD + kk * 16 + 2 * t;
+            float2* o = op + (kk * 2 + mi) * 4;
+            o[0] = *reinterpret_cast<const float2*>(r);
+            o[1] = *reinterpret_cast<const float2*>(r + 8 * kStageLD);
+            o[2] = *reinterpret_cast<const float2*>(r + 8);
+            o[3] = *reinterpret_cast<const float2*>(r + 8 * kStageLD + 8);
+        }
 }
 
 // Fragment coordinates (m16n8k16): g = lane / 4, t = lane % 4;
@@ -588,10 +653,12 @@ __device__ __forceinline__ float2 ldcg_f2(const float* p) {
 // Block job: G[P_u, P_w] <- Q_u^T G[P_u, P_w] Q_w and its mirror.  B of the
 // first product is read through the symmetry, B[k][n] = G[P_w(n)][P_u(k)],
 // so every fragment is a consecutive pair.  On the diagonal (u == w) only the
-// upper triangle is written, to both halves.
-template <bool kS>
+// upper triangle is written, to both halves.  Staged (kSt): the B fragments
+// come in op, op[(kk * 4 + nj) * 2 + h] = B[16kk + 2t + 8h][8nj + g].
+template <bool kS, bool kSt>
 __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restrict__ Qu,
-                          const uint32_t* __restrict__ Qw, int ui, int uj, int wi, int wj) {
+                          const uint32_t* __restrict__ Qw, int ui, int uj, int wi, int wj,
+                          const float2 (&op)[16]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const bool diag = ui == wi && uj == wj;
     float acc[2][4][4];
@@ -608,21 +675,22 @@ __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restr
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi) {
             const int m = mi * 16 + g, kp = kk * 8 + t;
-            ah[mi][0] = ldq<kS>(Qu + m * 16 + kp);
-            ah[mi][1] = ldq<kS>(Qu + (m + 8) * 16 + kp);
-            ah[mi][2] = ldq<kS>(Qu + m * 16 + kp + 4);
-            ah[mi][3] = ldq<kS>(Qu + (m + 8) * 16 + kp + 4);
-            al[mi][0] = ldq<kS>(Qu + kQWords + m * 16 + kp);
-            al[mi][1] = ldq<kS>(Qu + kQWords + (m + 8) * 16 + kp);
-            al[mi][2] = ldq<kS>(Qu + kQWords + m * 16 + kp + 4);
-            al[mi][3] = ldq<kS>(Qu + kQWords + (m + 8) * 16 + kp + 4);
+            ah[mi][0] = ldq<kS, kSt>(Qu, m * 16 + kp);
+            ah[mi][1] = ldq<kS, kSt>(Qu, (m + 8) * 16 + kp);
+            ah[mi][2] = ldq<kS, kSt>(Qu, m * 16 + kp + 4);
+            ah[mi][3] = ldq<kS, kSt>(Qu, (m + 8) * 16 + kp + 4);
+            al[mi][0] = ldq<kS, kSt>(Qu, kQWords + m * 16 + kp);
+            al[mi][1] = ldq<kS, kSt>(Qu, kQWords + (m + 8) * 16 + kp);
+            al[mi][2] = ldq<kS, kSt>(Qu, kQWords + m * 16 + kp + 4);
+            al[mi][3] = ldq<kS, kSt>(Qu, kQWords + (m + 8) * 16 + kp + 4);
         }
         const int k = kk * 16 + 2 * t;
         const int c0 = gidx(ui, uj, k), c1 = gidx(ui, uj, k + 8);
 #pragma unroll
         for (int nj = 0; nj < 4; ++nj) {
             const float* row = G + (int64_t)gidx(wi, wj, nj * 8 + g) * Mp;
-            const float2 v0 = ldcg_f2(row + c0), v1 = ldcg_f2(row + c1);
+            const float2 v0 = kSt ? op[(kk * 4 + nj) * 2] : ldcg_f2(row + c0);
+            const float2 v1 = kSt ? op[(kk * 4 + nj) * 2 + 1] : ldcg_f2(row + c1);
             uint32_t bh0, bl0, bh1, bl1;
             split_h2(v0.x, v0.y, bh0, bl0);
             split_h2(v1.x, v1.y, bh1, bl1);
@@ -654,9 +722,9 @@ __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restr
 #pragma unroll
         for (int nj = 0; nj < 4; ++nj) {
             const int n = nj * 8 + g, kp = kk * 8 + t;
-            const uint32_t bh0 = ldq<kS>(Qw + n * 16 + kp), bh1 = ldq<kS>(Qw + n * 16 + kp + 4);
-            const uint32_t bl0 = ldq<kS>(Qw + kQWords + n * 16 + kp);
-            const uint32_t bl1 = ldq<kS>(Qw + kQWords + n * 16 + kp + 4);
+            const uint32_t bh0 = ldq<kS, kSt>(Qw, n * 16 + kp), bh1 = ldq<kS, kSt>(Qw, n * 16 + kp + 4);
+            const uint32_t bl0 = ldq<kS, kSt>(Qw, kQWords + n * 16 + kp);
+            const uint32_t bl1 = ldq<kS, kSt>(Qw, kQWords + n * 16 + kp + 4);
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi) mma_split(out[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
         }
@@ -691,10 +759,12 @@ __device__ void job_block(float* __restrict__ G, int Mp, const uint32_t* __restr
         }
 }
 
-// Column job: V[r0..r0+31, P_u] <- V[r0..r0+31, P_u] Q_u.
-template <bool kS>
+// Column job: V[r0..r0+31, P_u] <- V[r0..r0+31, P_u] Q_u.  Staged (kSt): the
+// A fragments come in op, op[(kk * 2 + mi) * 4 + q] = rows 16mi + g (+8 for
+// q odd), columns 16kk + 2t (+8 for q >= 2).
+template <bool kS, bool kSt>
 __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restrict__ Qu, int ui,
-                          int uj, int r0) {
+                          int uj, int r0, const float2 (&op)[16]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     float out[2][4][4];
 #pragma unroll
@@ -712,8 +782,9 @@ __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restr
         for (int mi = 0; mi < 2; ++mi) {
             const float* ra = V + (int64_t)(r0 + mi * 16 + g) * Mp;
             const float* rb = ra + 8 * (int64_t)Mp;
-            const float2 x0 = ldcg_f2(ra + c0), x1 = ldcg_f2(rb + c0);
-            const float2 x2 = ldcg_f2(ra + c1), x3 = ldcg_f2(rb + c1);
+            const float2* o = op + (kk * 2 + mi) * 4;
+            const float2 x0 = kSt ? o[0] : ldcg_f2(ra + c0), x1 = kSt ? o[1] : ldcg_f2(rb + c0);
+            const float2 x2 = kSt ? o[2] : ldcg_f2(ra + c1), x3 = kSt ? o[3] : ldcg_f2(rb + c1);
             split_h2(x0.x * kQScale, x0.y * kQScale, ah[mi][0], al[mi][0]);
             split_h2(x1.x * kQScale, x1.y * kQScale, ah[mi][1], al[mi][1]);
             split_h2(x2.x * kQScale, x2.y * kQScale, ah[mi][2], al[mi][2]);
@@ -722,9 +793,9 @@ __device__ void job_vcols(float* __restrict__ V, int Mp, const uint32_t* __restr
 #pragma unroll
         for (int nj = 0; nj < 4; ++nj) {
             const int n = nj * 8 + g, kp = kk * 8 + t;
-            const uint32_t bh0 = ldq<kS>(Qu + n * 16 + kp), bh1 = ldq<kS>(Qu + n * 16 + kp + 4);
-            const uint32_t bl0 = ldq<kS>(Qu + kQWords + n * 16 + kp);
-            const uint32_t bl1 = ldq<kS>(Qu + kQWords + n * 16 + kp + 4);
+            const uint32_t bh0 = ldq<kS, kSt>(Qu, n * 16 + kp), bh1 = ldq<kS, kSt>(Qu, n * 16 + kp + 4);
+            const uint32_t bl0 = ldq<kS, kSt>(Qu, kQWords + n * 16 + kp);
+            const uint32_t bl1 = ldq<kS, kSt>(Qu, kQWords + n * 16 + kp + 4);
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi) mma_split(out[mi][nj], ah[mi], al[mi], bh0, bh1, bl0, bl1);
         }
@@ -757,8 +828,8 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
 }
 
 template <int K>
-__device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp, int* rq, int* act,
-                            float tol, float floor_abs, int& rotated, int wi, int bar, bool cross) {
+__device__ bool group_sweep(float* sub, float* Q, float4* rot, int* act, float tol, float floor_abs,
+                            int& rotated, int wi, int bar, bool cross) {
     constexpr int LD = J4Smem::LD;
     constexpr int NU = kB / K;                 // pairs per warp per pass
     constexpr int HB = NU > 8 ? 8 : NU;        // pairs held in registers at once
@@ -808,7 +879,7 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
                     fq = q;
                     rotated = 1;
                 }
-                rc[lane] = c; rs[lane] = sn; rp[lane] = p; rq[lane] = q;
+                rot[lane] = make_float4(c, sn, __int_as_float(p), __int_as_float(q));
             }
             // a round without any rotation leaves sub and Q unchanged.  The
             // flag alternates between two slots by round parity: a warp still
@@ -828,8 +899,10 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
         for (int i = 0; i < 256 / (32 * K); ++i) {
             const int b = (wi + K * i) * 32 + lane;
             const int u = b >> 4, w = b & 15;
-            const float cu = rc[u], su = rs[u], cw = rc[w], sw = rs[w];
-            const int pu = rp[u], qu = rq[u], pw = rp[w], qw = rq[w];
+            const float4 ru = rot[u], rw = rot[w];
+            const float cu = ru.x, su = ru.y, cw = rw.x, sw = rw.y;
+            const int pu = __float_as_int(ru.z), qu = __float_as_int(ru.w);
+            const int pw = __float_as_int(rw.z), qw = __float_as_int(rw.w);
             const float x11 = sub[pu * LD + pw], x12 = sub[pu * LD + qw];
             const float x21 = sub[qu * LD + pw], x22 = sub[qu * LD + qw];
             const float y11 = cu * x11 - su * x21, y21 = su * x11 + cu * x21;
@@ -845,8 +918,8 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
             int pu[HB], qu[HB];
 #pragma unroll
             for (int v = 0; v < HB; ++v) {
-                const int u = wi + (h + v) * K;
-                cu[v] = rc[u]; su[v] = rs[u]; pu[v] = rp[u]; qu[v] = rq[u];
+                const float4 ru = rot[wi + (h + v) * K];
+                cu[v] = ru.x; su[v] = ru.y; pu[v] = __float_as_int(ru.z); qu[v] = __float_as_int(ru.w);
             }
 #pragma unroll
             for (int v = 0; v < HB; ++v) { x[v] = Q[lane * LD + pu[v]]; y[v] = Q[lane * LD + qu[v]]; }
@@ -867,9 +940,8 @@ __device__ bool group_sweep(float* sub, float* Q, float* rc, float* rs, int* rp,
 // Load, solve and publish pair u with a group of K warps.
 template <int K>
 __device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step, int u, float* sub,
-                           float* Q, float* rc, float* rs, int* rp, int* rq, int* act, float tol,
-                           float floor_abs, int& rotated, int wi, int bar,
-                           uint32_t* __restrict__ qbuf, int* __restrict__ ident) {
+                           float* Q, float4* rot, int* act, float tol, float floor_abs, int& rotated,
+                           int wi, int bar, uint32_t* __restrict__ qbuf, int* __restrict__ ident) {
     constexpr int LD = J4Smem::LD;
     const int lane = threadIdx.x & 31;
     int bi, bj;
@@ -882,8 +954,7 @@ __device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step
     // the pairs inside each index block are taken at the sweep's first step
     // (every block takes part in it), the pairs between the two blocks at
     // every step: each pair once per sweep at least
-    const bool moved = group_sweep<K>(sub, Q, rc, rs, rp, rq, act, tol, floor_abs, rotated, wi, bar,
-                                      step != 0);
+    const bool moved = group_sweep<K>(sub, Q, rot, act, tol, floor_abs, rotated, wi, bar, step != 0);
     if (wi == 0 && (threadIdx.x & 31) == 0) ident[u] = moved ? 0 : 1;
     uint32_t* qo = qbuf + (size_t)u * 2 * kQWords;
     for (int w = wi; w < kB; w += K) {
@@ -896,9 +967,126 @@ __device__ void solve_pair(const float* __restrict__ G, int Mp, int nb, int step
     group_bar(bar, 32 * K);
 }
 
+// The 256 pairs between the two index blocks of pair u (16 rounds; round r
+// pairs p < 16 with 16 + (p + r) mod 16) by one warp, the sub-problem in
+// registers.  Lane j holds column j of the sub-problem S and of Q.  The rows
+// of the second index block are shifted by one register after every round,
+// so that the partner row of row p is always register 16 + p: the row
+// rotations (R^T S) then use fixed registers, and the column rotations (S R,
+// Q R) take the partner lane's column by shuffles.  Diagonal entries are
+// tracked per lane (d_j) with the same update as the shared-memory solver
+// (a - t g, d + t g); the same threshold decides each rotation.  No named
+// barrier and no shared traffic but the round's 16 rotations (tab).
+__device__ void solve_cross_warp(const float* __restrict__ G, int Mp, int nb, int step, int u,
+                                 float tol, float floor_abs, int& rotated, uint32_t* __restrict__ qbuf,
+                                 int* __restrict__ ident, float2* tab) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool lo = lane < kB;
+    int bi, bj;
+    circle_pair(nb, step, u, bi, bj);
+    float sv[kB2], qv[kB2];
+    {
+        // column lane of S = row lane (S is symmetric in memory)
+        const float* row = G + (int64_t)gidx(bi, bj, lane) * Mp;
+#pragma unroll
+        for (int i = 0; i < kB; i += 4) {
+            const float4 a = __ldcg(reinterpret_cast<const float4*>(row + bi * kB + i));
+            const float4 b = __ldcg(reinterpret_cast<const float4*>(row + bj * kB + i));
+            sv[i] = a.x; sv[i + 1] = a.y; sv[i + 2] = a.z; sv[i + 3] = a.w;
+            sv[kB + i] = b.x; sv[kB + i + 1] = b.y; sv[kB + i + 2] = b.z; sv[kB + i + 3] = b.w;
+        }
+    }
+    float dg = __ldcg(G + (int64_t)gidx(bi, bj, lane) * Mp + gidx(bi, bj, lane));
+#pragma unroll
+    for (int i = 0; i < kB2; ++i) qv[i] = i == lane ? 1.f : 0.f;
+    const float tol2 = tol * tol;
+    bool moved = false;
+#pragma unroll 1
+    for (int r = 0; r < kB; ++r) {
+        const int partner = lo ? kB + ((lane + r) & (kB - 1)) : ((lane - kB - r) & (kB - 1));
+        // g = S[q][p] of pair p = lane: register 16 + p
+        float g;
+        {
+            float x8[8], x4[4], x2[2];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x8[k] = (lane & 1) ? sv[kB + 2 * k + 1] : sv[kB + 2 * k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x4[k] = (lane & 2) ? x8[2 * k + 1] : x8[2 * k];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) x2[k] = (lane & 4) ? x4[2 * k + 1] : x4[2 * k];
+            g = (lane & 8) ? x2[1] : x2[0];
+        }
+        const float dp = __shfl_sync(kFull, dg, partner);
+        float c = 1.f, sn = 0.f, tg = 0.f;
+        bool rot = false;
+        if (lo && fabsf(g) > floor_abs && g * g > tol2 * fabsf(dg * dp)) {
+            const float h = dp - dg;
+            const float rr = sqrtf(fmaf(h, h, 4.f * g * g));
+            float t = 2.f * fabsf(g) * __frcp_rn(fabsf(h) + rr);
+            if ((h < 0.f) != (g < 0.f)) t = -t;
+            const float x = fmaf(t, t, 1.f);
+            c = rsqrtf(x);
+            c = c * fmaf(-0.5f * x, c * c, 1.5f);
+            sn = t * c;
+            tg = t * g;
+            rot = true;
+        }
+        if (__ballot_sync(kFull, rot) != 0u) {    // uniform over the warp
+            moved = true;
+            const float cx = __shfl_sync(kFull, c, partner);
+            const float sx = __shfl_sync(kFull, sn, partner);
+            const float tgx = __shfl_sync(kFull, tg, partner);
+            // this lane's column: c col_p - s col_q (lane p) or s col_p + c col_q (lane q)
+            const float cm = lo ? c : cx, sm = lo ? -sn : sx;
+            dg = lo ? dg - tg : dg + tgx;
+            if (lo) tab[lane] = make_float2(c, sn);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < kB; ++k) {
+                const float2 cs = tab[k];
+                const float x = sv[k], y = sv[kB + k];
+                sv[k] = cs.x * x - cs.y * y;
+                sv[kB + k] = cs.y * x + cs.x * y;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < kB2; ++i) {
+                const float o = __shfl_sync(kFull, sv[i], partner);
+                sv[i] = fmaf(sm, o, cm * sv[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < kB2; ++i) {
+                const float o = __shfl_sync(kFull, qv[i], partner);
+                qv[i] = fmaf(sm, o, cm * qv[i]);
+            }
+        }
+        // next round: register 16 + p takes the row that register 16 + p + 1 held
+        const float s0 = sv[kB];
+#pragma unroll
+        for (int m = 0; m < kB - 1; ++m) sv[kB + m] = sv[kB + m + 1];
+        sv[kB2 - 1] = s0;
+    }
+    if (moved) rotated = 1;
+    if (lane == 0) ident[u] = moved ? 0 : 1;
+    // row n = lane of (2^14 Q)^T: words w = (Q[2w][n], Q[2w + 1][n]), hi then lo
+    uint32_t hw[kB], lw[kB];
+#pragma unroll
+    for (int w = 0; w < kB; ++w) split_h2(qv[2 * w] * kQScale, qv[2 * w + 1] * kQScale, hw[w], lw[w]);
+    uint4* qh = reinterpret_cast<uint4*>(qbuf + (size_t)u * 2 * kQWords + lane * kB);
+    uint4* ql = reinterpret_cast<uint4*>(qbuf + (size_t)u * 2 * kQWords + kQWords + lane * kB);
+#pragma unroll
+    for (int k = 0; k < kB / 4; ++k) {
+        qh[k] = make_uint4(hw[4 * k], hw[4 * k + 1], hw[4 * k + 2], hw[4 * k + 3]);
+        ql[k] = make_uint4(lw[4 * k], lw[4 * k + 1], lw[4 * k + 2], lw[4 * k + 3]);
+    }
+}
+
 // Solve one FP32 matrix with csize CTAs (rank crank); qbuf holds the np
-// published rotations (np x 2 x kQWords words).
-template <bool kCluster>
+// published rotations (np x 2 x kQWords words).  kSt: update jobs stage
+// their operands through shared memory (kStageBytes per warp after the
+// solve area) and the shared copy of the rotations is swizzled.
+template <bool kCluster, bool kSt>
 __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int Mp, int csize,
                                int crank, int max_sweeps, float tol, int32_t* __restrict__ sweeps_out,
                                uint32_t* __restrict__ qbuf, unsigned char* smem_raw) {
@@ -959,7 +1147,7 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     const int kgrp = nmine >= kW4 ? 1 : nmine >= 4 ? 2 : nmine >= 2 ? 4 : 8;
     const int ngroups = kW4 / kgrp, grp = warp / kgrp, wi = warp % kgrp;
     int* ident = reinterpret_cast<int*>(qbuf + (size_t)np * 2 * kQWords);   // np flags
-    const bool qsmem = ((size_t)np * 2 * kQWords + np) * sizeof(uint32_t) <= J4Smem::bytes;
+    const bool qsmem = ((size_t)np * 2 * kQWords + np) * sizeof(uint32_t) <= J4Smem::solve_bytes;
     const int nblk = np * (np + 1) / 2;
     const int rtiles = Mp / kB2;
     const int njobs = nblk + np * rtiles;
@@ -970,20 +1158,27 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
         for (int step = 0; step < nb - 1; ++step) {
             // pair solves: the CTA's pairs u = crank + t csize go to groups of
             // kgrp warps; each group publishes (2^14 Q)^T (hi, lo) of its pairs
-            for (int t = grp; t < nmine; t += ngroups) {
+            // steps after the first: with at least 4 pairs per CTA, one warp
+            // per pair in registers; otherwise (and at the first step, which
+            // also takes the pairs inside each index block) groups of kgrp
+            // warps in shared memory
+            const bool by_warp = step != 0 && kgrp <= 2;
+            if (by_warp) {
+                float2* tab = reinterpret_cast<float2*>(smem_raw + J4Smem::per_warp * warp);
+                for (int t = warp; t < nmine; t += kW4)
+                    solve_cross_warp(G, Mp, nb, step, crank + t * csize, tol, floor_abs, rotated, qbuf, ident, tab);
+            }
+            for (int t = grp; t < nmine && !by_warp; t += ngroups) {
                 const int u = crank + t * csize;
                 float* gsub = reinterpret_cast<float*>(smem_raw + J4Smem::per_warp * grp);
                 float* gQ = gsub + kB2 * LD;
-                float* grc = gQ + kB2 * LD;
-                float* grs = grc + kB;
-                int* grp_p = reinterpret_cast<int*>(grs + kB);
-                int* grp_q = grp_p + kB;
-                int* gact = grp_q + kB;
+                float4* grot = reinterpret_cast<float4*>(gQ + kB2 * LD);
+                int* gact = reinterpret_cast<int*>(grot + kB);
                 switch (kgrp) {
-                    case 1: solve_pair<1>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
-                    case 2: solve_pair<2>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
-                    case 4: solve_pair<4>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
-                    default: solve_pair<8>(G, Mp, nb, step, u, gsub, gQ, grc, grs, grp_p, grp_q, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    case 1: solve_pair<1>(G, Mp, nb, step, u, gsub, gQ, grot, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    case 2: solve_pair<2>(G, Mp, nb, step, u, gsub, gQ, grot, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    case 4: solve_pair<4>(G, Mp, nb, step, u, gsub, gQ, grot, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
+                    default: solve_pair<8>(G, Mp, nb, step, u, gsub, gQ, grot, gact, tol, floor_abs, rotated, wi, 1 + grp, qbuf, ident); break;
                 }
             }
             owner_sync<kCluster>();
@@ -995,42 +1190,90 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                 uint32_t* qs = reinterpret_cast<uint32_t*>(smem_raw);
                 const int nw = np * 2 * kQWords;
                 for (int w = threadIdx.x; w < nw / 4; w += kJT4)
-                    reinterpret_cast<uint4*>(qs)[w] = __ldcg(reinterpret_cast<const uint4*>(qbuf) + w);
+                    reinterpret_cast<uint4*>(qs)[kSt ? w ^ ((w >> 3) & 3) : w] =
+                        __ldcg(reinterpret_cast<const uint4*>(qbuf) + w);
                 for (int w = threadIdx.x; w < np; w += kJT4) qs[nw + w] = (uint32_t)__ldcg(ident + w);
                 __syncthreads();
                 qsrc = qs;
                 isrc = reinterpret_cast<const int*>(qs + nw);
             }
-            for (int j = gwarp; j < njobs; j += nwarps) {
-                int u, w2 = 0;
+            auto ident_of = [&](int u) { return qsmem ? isrc[u] != 0 : __ldcg(ident + u) != 0; };
+            // job j: block (u, w2) of the upper triangle when j < nblk, else
+            // the column tile at rows r0 of P_u
+            auto decode = [&](int j, int& u, int& w2, int& r0) {
                 if (j < nblk) {
                     int r = j;
                     u = 0;
                     while (r >= np - u) { r -= np - u; ++u; }
                     w2 = u + r;
-                    // both rotations the identity: the block does not change
-                    const bool id_u = qsmem ? isrc[u] != 0 : __ldcg(ident + u) != 0;
-                    const bool id_w = qsmem ? isrc[w2] != 0 : __ldcg(ident + w2) != 0;
-                    if (id_u && id_w) continue;
-                    int ui, uj, wi2, wj;
-                    circle_pair(nb, step, u, ui, uj);
+                    r0 = 0;
+                    return true;
+                }
+                const int r = j - nblk;
+                u = r / rtiles;
+                w2 = u;
+                r0 = (r % rtiles) * kB2;
+                return false;
+            };
+            // a block whose two rotations are the identity (or a tile whose
+            // one is) does not change
+            auto next_job = [&](int j) {
+                for (; j < njobs; j += nwarps) {
+                    int u, w2, r0;
+                    const bool blk = decode(j, u, w2, r0);
+                    if (!(ident_of(u) && (!blk || ident_of(w2)))) break;
+                }
+                return j;
+            };
+            auto run_job = [&](bool blk, int u, int w2, int r0, const float2 (&op)[16]) {
+                int ui, uj;
+                circle_pair(nb, step, u, ui, uj);
+                const uint32_t* qu = qsrc + (size_t)u * 2 * kQWords;
+                if (blk) {
+                    int wi2, wj;
                     circle_pair(nb, step, w2, wi2, wj);
-                    if (qsmem)
-                        job_block<true>(G, Mp, qsrc + (size_t)u * 2 * kQWords, qsrc + (size_t)w2 * 2 * kQWords,
-                                        ui, uj, wi2, wj);
-                    else
-                        job_block<false>(G, Mp, qsrc + (size_t)u * 2 * kQWords, qsrc + (size_t)w2 * 2 * kQWords,
-                                         ui, uj, wi2, wj);
+                    const uint32_t* qw = qsrc + (size_t)w2 * 2 * kQWords;
+                    if (qsmem) job_block<true, kSt>(G, Mp, qu, qw, ui, uj, wi2, wj, op);
+                    else job_block<false, kSt>(G, Mp, qu, qw, ui, uj, wi2, wj, op);
                 } else {
-                    const int r = j - nblk;
-                    u = r / rtiles;
-                    if (qsmem ? isrc[u] != 0 : __ldcg(ident + u) != 0) continue;
-                    int ui, uj;
+                    if (qsmem) job_vcols<true, kSt>(V, Mp, qu, ui, uj, r0, op);
+                    else job_vcols<false, kSt>(V, Mp, qu, ui, uj, r0, op);
+                }
+            };
+            if constexpr (kSt) {
+                // the copy of job j + 1's operand runs while job j computes
+                float* stg = reinterpret_cast<float*>(smem_raw + J4Smem::solve_bytes + (size_t)warp * kStageBytes);
+                auto issue = [&](int j) {
+                    int u, w2, r0;
+                    const bool blk = decode(j, u, w2, r0);
+                    int ui, uj, wi2 = 0, wj = 0;
                     circle_pair(nb, step, u, ui, uj);
-                    if (qsmem)
-                        job_vcols<true>(V, Mp, qsrc + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
-                    else
-                        job_vcols<false>(V, Mp, qsrc + (size_t)u * 2 * kQWords, ui, uj, (r % rtiles) * kB2);
+                    if (blk) circle_pair(nb, step, w2, wi2, wj);
+                    stage_rows(stg, blk ? G : V, Mp, ui, uj, blk, wi2, wj, r0);
+                };
+                int j = next_job(gwarp);
+                if (j < njobs) issue(j);
+                while (j < njobs) {
+                    const int jn = next_job(j + nwarps);
+                    float2 op[16];
+                    cp_async_wait_all();
+                    __syncwarp();
+                    if (j < nblk) frag_block(stg, op);
+                    else frag_vcols(stg, op);
+                    __syncwarp();
+                    if (jn < njobs) issue(jn);
+                    int u, w2, r0;
+                    const bool blk = decode(j, u, w2, r0);
+                    run_job(blk, u, w2, r0, op);
+                    j = jn;
+                }
+            } else {
+                const float2 none[16] = {};
+                for (int j = gwarp; j < njobs; j += nwarps) {
+                    int u, w2, r0;
+                    const bool blk = decode(j, u, w2, r0);
+                    if (ident_of(u) && (!blk || ident_of(w2))) continue;
+                    run_job(blk, u, w2, r0, none);
                 }
             }
             // (the next step's solves overwrite the shared copy: every warp of
@@ -1075,13 +1318,14 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     if (crank == 0 && threadIdx.x == 0) *sweeps_out = converged ? sweep : -sweep;
 }
 
+template <bool kSt>
 __global__ void __launch_bounds__(kJT4, 2)
 k_jacobi4(float* __restrict__ Gall, float* __restrict__ Vall, int Mp, int csize, int max_sweeps,
           float tol, int32_t* __restrict__ sweeps_out, uint32_t* __restrict__ qall) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int crank = (int)cg::this_cluster().block_rank();
     const int mat = blockIdx.x / csize;
-    jacobi4_matrix<true>(Gall + (int64_t)mat * Mp * Mp, Vall + (int64_t)mat * Mp * Mp, Mp, csize,
+    jacobi4_matrix<true, kSt>(Gall + (int64_t)mat * Mp * Mp, Vall + (int64_t)mat * Mp * Mp, Mp, csize,
                          crank, max_sweeps, tol, sweeps_out + mat,
                          qall + (size_t)mat * jwork_words(Mp), smem_raw);
 }
@@ -1098,7 +1342,7 @@ k_jacobi4_items(const JacobiItem* __restrict__ items, int nitems, int* __restric
         __syncthreads();
         if (it >= nitems) break;
         const JacobiItem w = items[it];
-        jacobi4_matrix<false>(static_cast<float*>(w.G), static_cast<float*>(w.Vt), w.Mp, 1, 0,
+        jacobi4_matrix<false, true>(static_cast<float*>(w.G), static_cast<float*>(w.Vt), w.Mp, 1, 0,
                               w.max_sweeps > 0 ? w.max_sweeps : max_sweeps, tol, w.sweeps,
                               static_cast<uint32_t*>(w.work), smem_raw);
         __syncthreads();
@@ -1110,22 +1354,29 @@ k_jacobi4_items(const JacobiItem* __restrict__ items, int nitems, int* __restric
 // maximum active clusters.
 constexpr int kSolve4 = 4;
 
-// Whether a cluster of cs CTAs of the FP32 solver can be resident.
-bool cluster_fits4(int cs) {
-    if (cs > 8 && cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                      cudaSuccess) {
+// The FP32 solver for several matrices stages its job operands (the copies
+// hide L2 latency over many jobs per warp); a single matrix (the merge) has
+// a few jobs per warp and runs the direct form.
+using Jacobi4Kernel = void (*)(float*, float*, int, int, int, float, int32_t*, uint32_t*);
+Jacobi4Kernel jacobi4_kernel(bool staged) { return staged ? k_jacobi4<true> : k_jacobi4<false>; }
+
+// Clusters of cs CTAs of the FP32 solver that can be resident at once (0 if
+// none can).
+int active_clusters4(int cs, bool staged) {
+    const Jacobi4Kernel kern = jacobi4_kernel(staged);
+    const size_t smem = J4Smem::bytes(staged);
+    if (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    if (cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)J4Smem::bytes) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs, 1, 1);
     cfg.blockDim = dim3(kJT4, 1, 1);
-    cfg.dynamicSmemBytes = J4Smem::bytes;
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cs;
@@ -1134,45 +1385,21 @@ bool cluster_fits4(int cs) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi4, &cfg) != cudaSuccess || nclusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return true;
+    return nclusters;
 }
 
-int pick_cluster4(int nmat, int Mp) {
+int pick_cluster4(int nmat, int Mp, bool staged) {
     const int np = Mp / kB2;
     const int64_t jobs = (int64_t)np * (np + 1) / 2 + (int64_t)np * (Mp / kB2);
     int best = -1;
     double best_cost = 1e300;
     for (int cs = 1; cs <= kMaxCluster; cs *= 2) {
-        if (cs > 8 && cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                          cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)J4Smem::bytes) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)cs, 1, 1);
-        cfg.blockDim = dim3(kJT4, 1, 1);
-        cfg.dynamicSmemBytes = J4Smem::bytes;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi4, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        const int nclusters = active_clusters4(cs, staged);
+        if (nclusters < 1) continue;
         const int nw = cs * kW4;
         const double solves = (double)((np + nw - 1) / nw);
         const double per_warp = (double)(jobs + nw - 1) / nw;
@@ -1253,20 +1480,22 @@ cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double 
         if (!work) return cudaErrorInvalidValue;
         // a requested cluster size (1, 2, 4, 8 or 16) that cannot be launched
         // falls back to the occupancy model's choice
+        const bool staged = nmat > 1;
+        const Jacobi4Kernel kern = jacobi4_kernel(staged);
         int csize = -1;
         if (cluster >= 1 && cluster <= kMaxCluster && (cluster & (cluster - 1)) == 0 &&
-            cluster_fits4(cluster))
+            active_clusters4(cluster, staged) >= 1)
             csize = cluster;
-        if (csize < 1) csize = pick_cluster4(nmat, Mp);
+        if (csize < 1) csize = pick_cluster4(nmat, Mp, staged);
         if (csize < 1) return cudaErrorInvalidConfiguration;
         if (csize > 8)
-            RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)J4Smem::bytes));
+            RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        RK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)J4Smem::bytes(staged)));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nmat * csize), 1, 1);
         cfg.blockDim = dim3(kJT4, 1, 1);
-        cfg.dynamicSmemBytes = J4Smem::bytes;
+        cfg.dynamicSmemBytes = J4Smem::bytes(staged);
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1275,7 +1504,7 @@ cudaError_t launch_jacobi(T* G, T* Vt, int nmat, int Mp, int max_sweeps, double 
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_jacobi4, (float*)G, (float*)Vt, Mp, csize, max_sweeps,
+        return cudaLaunchKernelEx(&cfg, kern, (float*)G, (float*)Vt, Mp, csize, max_sweeps,
                                   (float)tol, sweeps, static_cast<uint32_t*>(work));
     } else {
         const int csize = pick_cluster<T>(nmat, npairs);
@@ -1312,12 +1541,12 @@ cudaError_t launch_jacobi_items(const JacobiItem* items, int nitems, int max_mp,
     if constexpr (sizeof(T) == 4) {
         if (max_mp % kB2 != 0 || max_mp < kB2 || max_mp > kMaxM) return cudaErrorInvalidValue;
         RK_CUDA_TRY(cudaFuncSetAttribute(k_jacobi4_items, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)J4Smem::bytes));
+                                         (int)J4Smem::bytes(true)));
         RK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi4_items, kJT4,
-                                                                  J4Smem::bytes));
+                                                                  J4Smem::bytes(true)));
         const int grid = std::max(1, std::min(nitems, sms * std::max(per_sm, 1)));
         RK_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(int), s));
-        k_jacobi4_items<<<grid, kJT4, J4Smem::bytes, s>>>(items, nitems, next, max_sweeps, (float)tol);
+        k_jacobi4_items<<<grid, kJT4, J4Smem::bytes(true), s>>>(items, nitems, next, max_sweeps, (float)tol);
         return cudaGetLastError();
     } else {
         const int ppc = max_mp / kB2;
