@@ -69,7 +69,14 @@ __device__ __forceinline__ void rr_pair(int n, int r, int u, int& a, int& b) {
 // runs of linked positions are the clusters, cut into pieces of at most
 // kRRMax at their largest gaps.  cid[i] = the piece of index i, -1 outside
 // every piece.
-// One CTA of 1024 threads per matrix (Mp <= 1024).
+// One CTA of 1024 threads per matrix (Mp <= 1024).  The O(M^2) passes avoid
+// FP64 arithmetic, whose rate is a small fraction of the other pipes': the
+// scan limit of row a is the power of two
+//   2^(max_c max(e(S_ac) - 1021, e(lam_c) + e(B_ac) - 2043)) >= rowmax[a]
+// (e = biased IEEE exponent; |x| < 2^(e(x) - 1022)), at most 4x the exact
+// maximum; pairs beyond the exact maximum fail the link test anyway, so the
+// clusters are the same.  The scan runs a warp per position, 32 candidates
+// per ballot, with the exact FP64 test.
 __global__ void __launch_bounds__(1024)
 k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp, double kappa,
           int stagger, double* __restrict__ lam, double* __restrict__ lmax_out,
@@ -78,7 +85,8 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
     __shared__ double key[kMaxM];
     __shared__ int id[kMaxM];
     __shared__ int reach[kMaxM];
-    __shared__ double rowmax[kMaxM];
+    __shared__ int rowexp[kMaxM];
+    __shared__ int elam[kMaxM];
     __shared__ double wmax[32];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int64_t mm = (int64_t)Mp * Mp;
@@ -91,6 +99,7 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         const double bii = Bb[(int64_t)i * Mp + i];
         const double l = bii > 0.0 ? Sb[(int64_t)i * Mp + i] / bii : 0.0;
         L[i] = l;
+        elam[i] = (__double2hiint(l) >> 20) & 0x7ff;
         cb[i] = -1;
         if (l == l) lm = fmax(lm, fabs(l));
     }
@@ -110,20 +119,22 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         lmax_out[b] = m;
     }
     __syncthreads();
-    // rowmax[a] = max_{c != a} |S_ac| + |lam_c| |B_ac|: bounds the link test of row a
+    // rowexp[a]: 2^rowexp[a] > max_{c != a} |S_ac| + |lam_c| |B_ac|, which
+    // bounds the link test of row a
     {
         const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
         for (int a = warp; a < M; a += nw) {
-            double m = 0.0;
+            int m = -4096;
+            const double* Sa = Sb + (int64_t)a * Mp;
+            const double* Ba = Bb + (int64_t)a * Mp;
             for (int c = lane; c < M; c += 32) {
                 if (c == a) continue;
-                const double lc = L[c];
-                const double v = fabs(Sb[(int64_t)a * Mp + c]) +
-                                 (lc == lc ? fabs(lc) : 0.0) * fabs(Bb[(int64_t)a * Mp + c]);
-                if (v == v) m = fmax(m, v);
+                const int es = (__double2hiint(Sa[c]) >> 20) & 0x7ff;
+                const int eb = (__double2hiint(Ba[c]) >> 20) & 0x7ff;
+                m = max(m, max(es - 1021, elam[c] + eb - 2043));
             }
-            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) rowmax[a] = m;
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) rowexp[a] = m;
         }
     }
     __syncthreads();
@@ -145,20 +156,35 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         }
     }
     int32_t* ord = order + (int64_t)b * Mp;
-    for (int q = tid; q < M; q += blockDim.x) {
-        ord[q] = id[q];
-        const int a = id[q];
-        const double lim = kappa * rowmax[a];    // no pair further than this links
-        int r = q;
-        for (int q2 = q + 1; q2 < M; ++q2) {
-            const double gap = key[q2] - key[q];
-            if (!(gap <= lim)) break;
-            const int c = id[q2];
-            const double crit = kappa * (fabs(Sb[(int64_t)a * Mp + c]) +
-                                         fabs(key[q2]) * fabs(Bb[(int64_t)a * Mp + c]));
-            if (gap <= crit) r = q2;
+    for (int q = tid; q < M; q += blockDim.x) ord[q] = id[q];
+    {
+        // reach[q] = the last position linked to q; keys are sorted, so the
+        // candidates within the limit are a prefix of q + 1, q + 2, ...
+        const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+        for (int q = warp; q < M; q += nw) {
+            const int a = id[q];
+            const double lim = kappa * ldexp(1.0, rowexp[a]);    // no pair further than this links
+            const double* Sa = Sb + (int64_t)a * Mp;
+            const double* Ba = Bb + (int64_t)a * Mp;
+            int r = q;
+            for (int base = q + 1; base < M; base += 32) {
+                const int q2 = base + lane;
+                bool in = false, link = false;
+                if (q2 < M) {
+                    const double gap = key[q2] - key[q];
+                    in = gap <= lim;
+                    if (in) {
+                        const int c = id[q2];
+                        const double crit = kappa * (fabs(Sa[c]) + fabs(key[q2]) * fabs(Ba[c]));
+                        link = gap <= crit;
+                    }
+                }
+                const unsigned lm = __ballot_sync(0xffffffffu, link);
+                if (lm != 0u) r = base + 31 - __clz(lm);
+                if (__ballot_sync(0xffffffffu, q2 < M && !in) != 0u) break;
+            }
+            if (lane == 0) reach[q] = r;
         }
-        reach[q] = r;
     }
     __syncthreads();
     if (tid == 0) {
@@ -475,6 +501,11 @@ k_rr_cols(double* __restrict__ Z0, double* __restrict__ Z1, int Mp,
 // first-order step does not correct but scrambles; when their gap is at the
 // level of the estimates' noise (long runs of repeated eigenvalues) the
 // mixing costs nothing.  R = I - B, written over B.
+// The numerator and the gap are formed in FP64 (both cancel); their quotient
+// is taken in FP32 after scaling both by a power of two near 1 / lmax: E is
+// applied through a product of three 8-bit slices (23 bits), and an FP64
+// division per entry would run on the FP64 pipe, whose rate is a small
+// fraction of the FP32 one.
 __global__ void k_rr_correction(double* __restrict__ B, const double* __restrict__ S, int Mp,
                                 const double* __restrict__ lam, const double* __restrict__ lmax,
                                 const int32_t* __restrict__ cid, double max_corr) {
@@ -483,18 +514,36 @@ __global__ void k_rr_correction(double* __restrict__ B, const double* __restrict
     const double* Sb = S + (int64_t)b * Mp * Mp;
     const double* L = lam + (int64_t)b * Mp;
     const int32_t* cb = cid + (int64_t)b * Mp;
-    const double tiny = 64.0 * 1.1102230246251565e-16 * lmax[b];
+    const double lm = lmax[b];
+    const double tiny = 64.0 * 1.1102230246251565e-16 * lm;
+    int ex = 0;
+    if (lm > 0.0 && lm <= DBL_MAX) frexp(lm, &ex);
+    const double sc = ldexp(1.0, -ex);        // sc * lmax in [0.5, 1)
+    const float fmax_corr = (float)max_corr;
     const int n = Mp * Mp;   // <= 2^20
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int i = e / Mp, j = e - i * Mp;
-        const double r = (i == j ? 1.0 : 0.0) - Bb[e];
-        const double gap = L[j] - L[i];
-        const int ci = cb[i];
-        const bool same = ci >= 0 && ci == cb[j];
-        double v = 0.5 * r;
-        if (i != j && !same && fabs(gap) > tiny) {
-            const double f = (Sb[e] + L[j] * r) / gap;
-            if (fabs(f) <= max_corr) v = f;
+        const double bij = Bb[e];
+        double v;
+        if (i == j) {
+            v = 0.5 * (1.0 - bij);
+        } else {
+            bool first_order = false;
+            const int ci = cb[i];
+            if (!(ci >= 0 && ci == cb[j])) {
+                const double lj = L[j];
+                const double gap = lj - L[i];
+                if (fabs(gap) > tiny) {
+                    // (S_ij + lam_j R_ij) / gap, R_ij = -B_ij
+                    const double num = fma(-lj, bij, Sb[e]);
+                    const float f = __double2float_rn(num * sc) / __double2float_rn(gap * sc);
+                    if (fabsf(f) <= fmax_corr) {
+                        v = (double)f;
+                        first_order = true;
+                    }
+                }
+            }
+            if (!first_order) v = -0.5 * bij;
         }
         Bb[e] = v;
     }

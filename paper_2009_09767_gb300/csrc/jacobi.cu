@@ -1162,7 +1162,7 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
             // per pair in registers; otherwise (and at the first step, which
             // also takes the pairs inside each index block) groups of kgrp
             // warps in shared memory
-            const bool by_warp = step != 0 && kgrp <= 2;
+            const bool by_warp = step != 0 && (!kSt || kgrp <= 2);
             if (by_warp) {
                 float2* tab = reinterpret_cast<float2*>(smem_raw + J4Smem::per_warp * warp);
                 for (int t = warp; t < nmine; t += kW4)
