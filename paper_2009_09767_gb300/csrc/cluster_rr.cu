@@ -61,6 +61,42 @@ __device__ __forceinline__ void rr_pair(int n, int r, int u, int& a, int& b) {
     if (a > b) { const int t = a; a = b; b = t; }
 }
 
+// rowexp[a]: 2^rowexp[a] > max_{c != a} |S_ac| + |lam_c| |B_ac| with
+// lam_c = S_cc / B_cc, from IEEE exponent fields alone (the FP64 pipe, a
+// small fraction of the others' rate, stays idle): with e(x) the biased
+// exponent, |x| < 2^(e(x) - 1022) and |S_cc / B_cc| < 2^(e(S_cc) - e(B_cc) + 1),
+// so the bound is at most 8x the maximum.  A CTA of 8 warps takes 32 rows
+// of one matrix, a warp a row at a time.
+__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+__global__ void __launch_bounds__(256)
+k_rr_rowexp(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp,
+            int32_t* __restrict__ rowexp) {
+    __shared__ int elam[kMaxM];     // |lam_c| < 2^(elam[c] - 1022)
+    const int b = blockIdx.y;
+    const int64_t mm = (int64_t)Mp * Mp;
+    const double* Sb = S + b * mm;
+    const double* Bb = B + b * mm;
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        // a zero or subnormal B_cc leaves no bound: scan the whole row
+        const int eb = exp_field(Bb[(int64_t)c * Mp + c]);
+        elam[c] = eb == 0 ? 4095 : exp_field(Sb[(int64_t)c * Mp + c]) - eb + 1023;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = blockIdx.x * 32 + warp; a < min(M, blockIdx.x * 32 + 32); a += 8) {
+        const double* Sa = Sb + (int64_t)a * Mp;
+        const double* Ba = Bb + (int64_t)a * Mp;
+        int m = -4096;
+        for (int c = lane; c < M; c += 32) {
+            if (c == a) continue;
+            m = max(m, max(exp_field(Sa[c]) - 1021, elam[c] + exp_field(Ba[c]) - 2043));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) rowexp[(int64_t)b * Mp + a] = m;
+    }
+}
+
 // Estimates lam_i = S_ii / B_ii (all Mp indices) and their largest magnitude;
 // then the clusters: sort the first M estimates; positions q < q2 are linked
 // when the first-order mixing estimate of the pair is not small,
@@ -69,24 +105,21 @@ __device__ __forceinline__ void rr_pair(int n, int r, int u, int& a, int& b) {
 // runs of linked positions are the clusters, cut into pieces of at most
 // kRRMax at their largest gaps.  cid[i] = the piece of index i, -1 outside
 // every piece.
-// One CTA of 1024 threads per matrix (Mp <= 1024).  The O(M^2) passes avoid
-// FP64 arithmetic, whose rate is a small fraction of the other pipes': the
-// scan limit of row a is the power of two
-//   2^(max_c max(e(S_ac) - 1021, e(lam_c) + e(B_ac) - 2043)) >= rowmax[a]
-// (e = biased IEEE exponent; |x| < 2^(e(x) - 1022)), at most 4x the exact
-// maximum; pairs beyond the exact maximum fail the link test anyway, so the
-// clusters are the same.  The scan runs a warp per position, 32 candidates
-// per ballot, with the exact FP64 test.
+// One CTA of 1024 threads per matrix (Mp <= 1024).  The scan limit of row a
+// is 2^rowexp[a] (k_rr_rowexp), at least the exact maximum of the link
+// test's right-hand side over the row: pairs beyond the exact maximum fail
+// the test anyway, so the clusters are those of the exact limit.  The scan
+// runs a warp per position, 32 candidates per ballot, with the exact FP64
+// test.
 __global__ void __launch_bounds__(1024)
 k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp, double kappa,
           int stagger, double* __restrict__ lam, double* __restrict__ lmax_out,
           int32_t* __restrict__ order, int32_t* __restrict__ cstart, int32_t* __restrict__ csize,
-          int32_t* __restrict__ ncl, int32_t* __restrict__ cid) {
+          int32_t* __restrict__ ncl, int32_t* __restrict__ cid, const int32_t* __restrict__ rowexp_g) {
     __shared__ double key[kMaxM];
     __shared__ int id[kMaxM];
     __shared__ int reach[kMaxM];
     __shared__ int rowexp[kMaxM];
-    __shared__ int elam[kMaxM];
     __shared__ double wmax[32];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int64_t mm = (int64_t)Mp * Mp;
@@ -99,7 +132,7 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         const double bii = Bb[(int64_t)i * Mp + i];
         const double l = bii > 0.0 ? Sb[(int64_t)i * Mp + i] / bii : 0.0;
         L[i] = l;
-        elam[i] = (__double2hiint(l) >> 20) & 0x7ff;
+        rowexp[i] = rowexp_g[(int64_t)b * Mp + i];
         cb[i] = -1;
         if (l == l) lm = fmax(lm, fabs(l));
     }
@@ -117,25 +150,6 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         double m = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
         lmax_out[b] = m;
-    }
-    __syncthreads();
-    // rowexp[a]: 2^rowexp[a] > max_{c != a} |S_ac| + |lam_c| |B_ac|, which
-    // bounds the link test of row a
-    {
-        const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-        for (int a = warp; a < M; a += nw) {
-            int m = -4096;
-            const double* Sa = Sb + (int64_t)a * Mp;
-            const double* Ba = Bb + (int64_t)a * Mp;
-            for (int c = lane; c < M; c += 32) {
-                if (c == a) continue;
-                const int es = (__double2hiint(Sa[c]) >> 20) & 0x7ff;
-                const int eb = (__double2hiint(Ba[c]) >> 20) & 0x7ff;
-                m = max(m, max(es - 1021, elam[c] + eb - 2043));
-            }
-            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) rowexp[a] = m;
-        }
     }
     __syncthreads();
     // bitonic sort ascending on (key, id)
@@ -501,11 +515,19 @@ k_rr_cols(double* __restrict__ Z0, double* __restrict__ Z1, int Mp,
 // first-order step does not correct but scrambles; when their gap is at the
 // level of the estimates' noise (long runs of repeated eigenvalues) the
 // mixing costs nothing.  R = I - B, written over B.
-// The numerator and the gap are formed in FP64 (both cancel); their quotient
-// is taken in FP32 after scaling both by a power of two near 1 / lmax: E is
-// applied through a product of three 8-bit slices (23 bits), and an FP64
-// division per entry would run on the FP64 pipe, whose rate is a small
-// fraction of the FP32 one.
+// The numerator and the gap are formed in FP64 (both cancel); the quotient
+// takes the approximate FP64 reciprocal (rcp.approx, relative error about
+// 2^-20) times the numerator: E is applied through a product of three 8-bit
+// slices (23 bits), and a correctly rounded FP64 division per entry would
+// cost several FP64 operations on a pipe whose rate is a small fraction of
+// the FP32 one.  The threshold tests compare the high words of the IEEE
+// patterns (monotone in the magnitude), again off the FP64 pipe.
+__device__ __forceinline__ double rcp_approx(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
 __global__ void k_rr_correction(double* __restrict__ B, const double* __restrict__ S, int Mp,
                                 const double* __restrict__ lam, const double* __restrict__ lmax,
                                 const int32_t* __restrict__ cid, double max_corr) {
@@ -514,12 +536,9 @@ __global__ void k_rr_correction(double* __restrict__ B, const double* __restrict
     const double* Sb = S + (int64_t)b * Mp * Mp;
     const double* L = lam + (int64_t)b * Mp;
     const int32_t* cb = cid + (int64_t)b * Mp;
-    const double lm = lmax[b];
-    const double tiny = 64.0 * 1.1102230246251565e-16 * lm;
-    int ex = 0;
-    if (lm > 0.0 && lm <= DBL_MAX) frexp(lm, &ex);
-    const double sc = ldexp(1.0, -ex);        // sc * lmax in [0.5, 1)
-    const float fmax_corr = (float)max_corr;
+    // high words of |x| compared as integers: |gap| > tiny, |f| <= max_corr
+    const int tiny_hi = __double2hiint(64.0 * 1.1102230246251565e-16 * lmax[b]) & 0x7fffffff;
+    const int corr_hi = __double2hiint(max_corr) & 0x7fffffff;
     const int n = Mp * Mp;   // <= 2^20
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int i = e / Mp, j = e - i * Mp;
@@ -533,12 +552,11 @@ __global__ void k_rr_correction(double* __restrict__ B, const double* __restrict
             if (!(ci >= 0 && ci == cb[j])) {
                 const double lj = L[j];
                 const double gap = lj - L[i];
-                if (fabs(gap) > tiny) {
+                if ((__double2hiint(gap) & 0x7fffffff) > tiny_hi) {
                     // (S_ij + lam_j R_ij) / gap, R_ij = -B_ij
-                    const double num = fma(-lj, bij, Sb[e]);
-                    const float f = __double2float_rn(num * sc) / __double2float_rn(gap * sc);
-                    if (fabsf(f) <= fmax_corr) {
-                        v = (double)f;
+                    const double f = fma(-lj, bij, Sb[e]) * rcp_approx(gap);
+                    if ((__double2hiint(f) & 0x7fffffff) <= corr_hi) {   // NaN fails
+                        v = f;
                         first_order = true;
                     }
                 }
@@ -557,8 +575,10 @@ cudaError_t launch_cluster_rr(const RRWork& w, int nmat, int Mp, double* X, doub
                               double* Tg, double* lam, double* lmax, cudaStream_t s) {
     if (nmat <= 0) return cudaSuccess;
     if (Mp > kMaxM || Mp % kRRTile != 0 || w.M > Mp) return cudaErrorInvalidValue;
+    k_rr_rowexp<<<dim3((unsigned)ceil_div(w.M, 32), nmat), 256, 0, s>>>(S, B, w.M, Mp, w.rowexp);
+    RK_CUDA_TRY(cudaGetLastError());
     k_rr_plan<<<nmat, 1024, 0, s>>>(S, B, w.M, Mp, w.kappa, w.stagger, lam, lmax, w.order,
-                                    w.cstart, w.csize, w.ncl, w.cid);
+                                    w.cstart, w.csize, w.ncl, w.cid, w.rowexp);
     RK_CUDA_TRY(cudaGetLastError());
     const int smem = (int)rr_smem_bytes();
     RK_CUDA_TRY(cudaFuncSetAttribute(k_rr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
