@@ -4,25 +4,30 @@
 // byte swizzle), tcgen05.mma with FP32 accumulators in tensor memory (TMEM).
 //
 // C = alpha A B^T (+ beta C) from the S bf16 slices of A (m rows) and B
-// (n rows).  Every slice pair (a, b) with a + b <= S + 1 gets its own TMEM
-// accumulator, so that its sum stays an exact integer in FP32: |s_a s_b| <=
-// 2^14, and 1024 products sum to at most 2^24.  Every 1024 k (and at the
-// end) the accumulators are read into registers and added, with the pair's
-// weight 2^(8 (S + 1 - a - b)), to one 64-bit integer per output.  The
-// result is bit for bit that of the mma.sync kernel of ozaki.cu: both form
-// the same integers and convert them once.
+// (n rows).  The slice pairs (a, b) with a + b <= S + 1 of one weight
+// w = a + b share a TMEM accumulator: w - 1 <= S pairs, each product
+// |s_a s_b| <= 2^14, so a run of up to 1024 / S in k sums to at most 2^24 and
+// stays an exact integer in FP32.  After every such run (and at the end) the
+// S accumulators are read into registers and added, with the weight
+// 2^(8 (S + 1 - w)), to one 64-bit integer per output.  The result is bit
+// for bit that of the mma.sync kernel of ozaki.cu: both form the same
+// integers and convert them once.
 //
-// CTA: 128 threads, output tile 128 x 32 (row i of the tile = TMEM lane i =
-// thread i at the drain), S (S + 1) / 2 <= 15 accumulators of 32 columns in
-// one 512-column TMEM allocation.  k runs in stages of 64 through NBUF shared
-// buffers.  Warp 0 runs the pipeline (lane 0 issues): each stage's tensor
-// copies (one per slice and operand, completion counted in bytes on the
-// buffer's "full" mbarrier) and, once they have landed, the stage's MMAs
-// (M = 128, N = 32, K = 16), committed to the buffer's "empty" mbarrier
-// before the buffer is refilled; the other warps wait for the drain.
-// Shared tiles are K-major with the 128-byte swizzle: rows of 64 bf16, 8-row
-// atoms of 1024 bytes; along k inside an atom the descriptor start advances
-// by 32 bytes per MMA.  Every wait is bounded: on expiry the CTA records an
+// CTA: 128 threads, output tile 128 x 64 (row i of the tile = TMEM lane i =
+// thread i at the drain), S accumulators of 64 columns in one 512-column
+// TMEM allocation.  The product is bound by bringing the operand slices into
+// shared memory, so the tile is as wide as the accumulators allow (fewer
+// operand bytes per output) and k runs in stages of 32 through NBUF shared
+// buffers (three stages in flight for S = 5, five for S = 3).  A product
+// with fewer than two such tiles per SM (one 512 x 512 matrix) takes tiles
+// 128 x 32 instead, for twice the CTAs.  Warp 0 runs
+// the pipeline (lane 0 issues): each stage's tensor copies (one per slice
+// and operand, completion counted in bytes on the buffer's "full" mbarrier)
+// and, once they have landed, the stage's MMAs (M = 128, N = 64, K = 16),
+// committed to the buffer's "empty" mbarrier before the buffer is refilled;
+// the other warps wait for the drain.  Shared tiles are K-major with the
+// 64-byte swizzle: rows of 32 bf16, 8-row atoms of 512 bytes; the second
+// MMA of a stage starts 32 bytes into the rows.  Every wait is bounded: on expiry the CTA records an
 // error, lets what it issued land (bounded), frees its TMEM and returns.
 #include <cuda.h>
 
@@ -36,50 +41,57 @@ namespace rk {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 32, TBK = 64;
-constexpr int kDrainK = 1024;                       // exact run of one accumulator
-constexpr int kStagesPerDrain = kDrainK / TBK;
+constexpr int TBM = 128, TBK = 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 1ll << 31;        // ~1 s of SM clock before a wait gives up
 
-template <int S>
+// TBN: tile width, 64 (fewer operand bytes per output) or 32 (twice the CTAs
+// for small products)
+template <int S, int TBN>
 struct TcSmem {
-    static constexpr int A_BYTES = TBM * TBK * 2;    // one slice tile, 16 KB
-    static constexpr int B_BYTES = TBN * TBK * 2;    // 4 KB
+    static constexpr int A_BYTES = TBM * TBK * 2;    // one slice tile, 8 KB
+    static constexpr int B_BYTES = TBN * TBK * 2;    // 4 or 2 KB
     static constexpr int STAGE = S * (A_BYTES + B_BYTES);
-    static constexpr int NBUF = S <= 3 ? 3 : 2;
+    static constexpr int NBUF = (200 * 1024) / STAGE;
     static constexpr int BAR = NBUF * STAGE;         // barriers after the buffers
     static constexpr int BYTES = BAR + 256 + 1024;   // + barriers, TMEM slot, alignment slack
+    // exact run of an accumulator: S pairs x k x 2^14 <= 2^24
+    static constexpr int STAGES_PER_DRAIN = (1024 / S) / TBK;
+    static_assert(S * TBN <= (int)kTmemCols, "accumulators fit the allocation");
+    static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 bytes apart (stride byte offset); the leading byte offset is unused
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row atoms
+// 512 bytes apart (stride byte offset); the leading byte offset is unused
 // for this layout (encoded 1)
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1 << 16;                     // leading byte offset (16 B, unused)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset
     d |= (uint64_t)1 << 46;                     // descriptor version of this architecture
-    d |= (uint64_t)2 << 61;                     // layout: 128-byte swizzle
+    d |= (uint64_t)4 << 61;                     // layout: 64-byte swizzle
     return d;
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
 // K-major, N = TBN, M = TBM
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
-                            ((uint32_t)(TBM >> 4) << 24);
+template <int TBN>
+constexpr uint32_t idesc_f16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+}
 
+template <int TBN>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                           uint32_t accumulate) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+        "l"(adesc), "l"(bdesc), "r"(idesc_f16<TBN>()), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
@@ -151,14 +163,14 @@ __device__ __forceinline__ int tc_exp(unsigned long long bits) {
     return (ef == 0 ? 1 : ef) - 1022;
 }
 
-template <int S>
+template <int S, int TBN>
 __global__ void __launch_bounds__(128, 1)
 k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m,
           int n, int64_t kpad, int64_t kc, const unsigned long long* __restrict__ amaxA,
           int rowsA_pad, const unsigned long long* __restrict__ amaxB, int rowsB_pad,
           double alpha, double beta, double* __restrict__ C, int64_t ldc, int64_t strideC,
           int64_t strideSplit, int nsplit, int sym, int* __restrict__ err) {
-    using L = TcSmem<S>;
+    using L = TcSmem<S, TBN>;
     constexpr int NB = L::NBUF;
     const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
     if (sym && j0 + TBN - 1 < i0) return;   // below the diagonal: mirrored from above
@@ -221,8 +233,8 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     int period = 0;
     const int lane = tid & 31;
-    for (int p0 = 0; p0 < nst; p0 += kStagesPerDrain, ++period) {
-        const int p1 = min(nst, p0 + kStagesPerDrain);
+    for (int p0 = 0; p0 < nst; p0 += L::STAGES_PER_DRAIN, ++period) {
+        const int p1 = min(nst, p0 + L::STAGES_PER_DRAIN);
         // warp 0 runs the copy/MMA loop with uniform control flow (every lane
         // waits, lane 0 issues); warps 1..3 go straight to the drain wait
         if (warp == 0 && !failed) {
@@ -241,20 +253,22 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     // descriptors of slice 1 at k = 0; a slice and a 16-k step move
                     // only the start-address field (16-byte units, no carry:
                     // shared addresses stay below 2^18)
-                    const uint64_t dA = umma_desc_sw128(sb);
-                    const uint64_t dB = umma_desc_sw128(sb + S * L::A_BYTES);
+                    const uint64_t dA = umma_desc_sw64(sb);
+                    const uint64_t dB = umma_desc_sw64(sb + S * L::A_BYTES);
+                    // the run's first MMA into accumulator w - 2 (pair (1, w - 1),
+                    // k = 0 of its first stage) overwrites it
                     const uint32_t first = it == p0 ? 0u : 1u;
 #pragma unroll
                     for (int a = 1; a <= S; ++a) {
 #pragma unroll
                         for (int bs = 1; a + bs <= S + 1; ++bs) {
-                            const int p = (a - 1) * (2 * S + 2 - a) / 2 + (bs - 1);
+                            const int q = a + bs - 2;
 #pragma unroll
                             for (int kk = 0; kk < TBK / 16; ++kk)
-                                umma_bf16(tbase + (uint32_t)(p * TBN),
+                                umma_bf16<TBN>(tbase + (uint32_t)(q * TBN),
                                           dA + (uint64_t)(((a - 1) * L::A_BYTES + kk * 32) >> 4),
                                           dB + (uint64_t)(((bs - 1) * L::B_BYTES + kk * 32) >> 4),
-                                          kk == 0 ? first : 1u);
+                                          (kk == 0 && a == 1) ? first : 1u);
                         }
                     }
                     umma_commit(empty0 + 8 * buf);
@@ -283,17 +297,16 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (failed) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         {
-            int p = 0;
 #pragma unroll 1
-            for (int a = 1; a <= S; ++a) {
-#pragma unroll 1
-                for (int bs = 1; a + bs <= S + 1; ++bs, ++p) {
-                    uint32_t r[32];
-                    tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * TBN), r);
-                    const int sh = 8 * (S + 1 - a - bs);
+            for (int q = 0; q < S; ++q) {            // weight w = q + 2
+                const int sh = 8 * (S - 1 - q);
 #pragma unroll
-                    for (int c = 0; c < TBN; ++c)
-                        acc[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
+                for (int h = 0; h < TBN / 32; ++h) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * TBN + h * 32), r);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        acc[h * 32 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
                 }
             }
         }
@@ -357,7 +370,7 @@ EncodeFn encode_fn() {
 }
 
 // the slices of an operand as a 3-d tensor (k, row, batch x slice) of
-// 16-bit elements; boxes of 64 k x box_rows rows, 128-byte swizzle
+// 16-bit elements; boxes of 32 k x box_rows rows, 64-byte swizzle
 cudaError_t slice_map(CUtensorMap* map, const OzOperand& op, int nb, int box_rows) {
     EncodeFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
@@ -368,28 +381,44 @@ cudaError_t slice_map(CUtensorMap* map, const OzOperand& op, int nb, int box_row
     const cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, op.slices, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int S>
+template <int S, int TBN>
 cudaError_t umma_gemm_t(int nb, int m, int n, int64_t kpad, int nsplit, const OzOperand& A,
                         const OzOperand& B, double alpha, double beta, double* C, int64_t ldc,
                         int64_t strideC, int64_t strideSplit, int sym, int* err, cudaStream_t s) {
-    constexpr int smem = TcSmem<S>::BYTES;
+    constexpr int smem = TcSmem<S, TBN>::BYTES;
     CUtensorMap ta, tb;
     RK_CUDA_TRY(slice_map(&ta, A, nb, TBM));
     RK_CUDA_TRY(slice_map(&tb, B, nb, TBN));
-    RK_CUDA_TRY(cudaFuncSetAttribute(k_oz_umma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RK_CUDA_TRY(cudaFuncSetAttribute(k_oz_umma<S, TBN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // split chunks on stage boundaries: a tensor copy past a chunk's end would
     // read the next chunk (past kpad it reads zeros)
     const int64_t kc = round_up(ceil_div(kpad, nsplit), TBK);
     dim3 grid((unsigned)ceil_div(n, TBN), (unsigned)ceil_div(m, TBM), (unsigned)(nb * nsplit));
-    k_oz_umma<S><<<grid, 128, smem, s>>>(ta, tb, m, n, kpad, kc, A.amax, A.rows_pad, B.amax,
-                                         B.rows_pad, alpha, beta, C, ldc, strideC, strideSplit,
-                                         nsplit, sym, err);
+    k_oz_umma<S, TBN><<<grid, 128, smem, s>>>(ta, tb, m, n, kpad, kc, A.amax, A.rows_pad, B.amax,
+                                              B.rows_pad, alpha, beta, C, ldc, strideC, strideSplit,
+                                              nsplit, sym, err);
     return cudaGetLastError();
+}
+
+// the wide tile unless that leaves fewer than two CTAs per SM
+template <int S>
+cudaError_t umma_gemm_s(int nb, int m, int n, int64_t kpad, int nsplit, const OzOperand& A,
+                        const OzOperand& B, double alpha, double beta, double* C, int64_t ldc,
+                        int64_t strideC, int64_t strideSplit, int sym, int* err, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    RK_CUDA_TRY(cudaGetDevice(&dev));
+    RK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t wide = ceil_div(n, 64) * ceil_div(m, TBM) * (int64_t)nb * nsplit;
+    if (wide >= 2 * (int64_t)sms)
+        return umma_gemm_t<S, 64>(nb, m, n, kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
+                                  strideSplit, sym, err, s);
+    return umma_gemm_t<S, 32>(nb, m, n, kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
+                              strideSplit, sym, err, s);
 }
 
 }  // namespace
@@ -399,14 +428,14 @@ cudaError_t launch_oz_gemm_tc(int nb, int m, int n, const OzOperand& A, const Oz
                               int sym, cudaStream_t s, int nsplit, int64_t strideSplit, int* err) {
     if (A.S != B.S || A.kpad != B.kpad || m > A.rows_pad || n > B.rows_pad || nsplit < 1)
         return cudaErrorInvalidValue;
-    if (A.rows_pad % TBM != 0 || B.rows_pad % TBN != 0 || A.kpad % 32 != 0)
+    if (A.rows_pad % TBM != 0 || B.rows_pad % 64 != 0 || A.kpad % TBK != 0)
         return cudaErrorInvalidValue;
     if (sym && m != n) return cudaErrorInvalidValue;
     if (nb <= 0 || m <= 0 || n <= 0) return cudaSuccess;
     if (A.S == 3)
-        return umma_gemm_t<3>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
+        return umma_gemm_s<3>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
                               strideSplit, sym, err, s);
-    return umma_gemm_t<5>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC, strideSplit,
+    return umma_gemm_s<5>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC, strideSplit,
                           sym, err, s);
 }
 
