@@ -142,10 +142,12 @@ class ClockSampler:
 
 
 # DRAM traffic of one block-Jacobi launch, as a stored note: dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of a 16-matrix launch (zipf_wide with 250k
-# columns), per matrix, with the hash of the kernel source it was taken on.  The line
-# reports it (scaled to the launch, labelled as stored) only while the source is unchanged.
-JACOBI_TRAFFIC = {"source_sha256_16": "none", "bytes_per_matrix": None}
+# dram__bytes_write.sum of a one-pass ncu capture of the 64-block launch of the full
+# zipf_wide SVD (25,626,356,736 + 3,863,602,304 bytes in 24.30 ms), with the hash of
+# the kernel source it was taken on.  The line reports it (labelled as stored) only for
+# that launch shape and while the source is unchanged.
+JACOBI_TRAFFIC = {"source_sha256_16": "c7f0548e86764d75", "blocks": 64,
+                  "bytes_per_launch": 25_626_356_736 + 3_863_602_304}
 
 
 def source_hash(rel: str) -> str:
@@ -159,12 +161,15 @@ def jacobi_flops(sweeps: np.ndarray, Mp: int) -> float:
     Mp/16 - 1 steps; a step with np = Mp/32 pairs updates the np (np + 1) / 2
     symmetric 32 x 32 blocks of G (two 32^3 products each), the eigenvector
     columns (np * Mp/32 products of 32^3) and solves np 32 x 32 sub-problems
-    (31 rounds x 16 rotations, each rotation 6 flops on 3 x 2 x 32 values)."""
+    (16 rotations a round, each 6 flops on 3 x 2 x 32 values: all 31 rounds
+    of a sub-problem at a sweep's first step, the 16 rounds of the pairs
+    between its two index blocks at the others)."""
     n_p = Mp // 32
     steps = Mp // 16 - 1
-    per_step = (n_p * (n_p + 1) / 2 * 2 * 2 * 32 ** 3 + n_p * (Mp // 32) * 2 * 32 ** 3
-                + n_p * 31 * 16 * 6 * 3 * 32)
-    return float(np.sum(np.abs(sweeps))) * steps * per_step
+    update = n_p * (n_p + 1) / 2 * 2 * 2 * 32 ** 3 + n_p * (Mp // 32) * 2 * 32 ** 3
+    rounds = 31 + 16 * (steps - 1)
+    per_sweep = steps * update + n_p * rounds * 16 * 6 * 3 * 32
+    return float(np.sum(np.abs(sweeps))) * per_sweep
 
 
 def accuracy_vs(s, U, s_ref, U_ref, gap=1e-3):
@@ -674,11 +679,11 @@ def main():
                 "achieved": achieved, "peak": fpk["tflops"], "unit": "TFLOP/s",
                 "frac": achieved / fpk["tflops"], "peak_source": fpk["source"],
                 "traffic": None, "kernel_ms": jac_ms, "algorithmic_flops": jac_flops}
-    if (JACOBI_TRAFFIC["bytes_per_matrix"] and source_hash("paper_2009_09767_gb300/csrc/jacobi.cu")
-            == JACOBI_TRAFFIC["source_sha256_16"]):
-        roofline["traffic"] = JACOBI_TRAFFIC["bytes_per_matrix"] * case.num_blocks
-        roofline["traffic_note"] = ("stored: ncu dram bytes of one 16-matrix launch of this "
-                                    "source, scaled by matrices to this launch")
+    if (case.num_blocks == JACOBI_TRAFFIC["blocks"] and args.precision == "mixed"
+            and source_hash("paper_2009_09767_gb300/csrc/jacobi.cu") == JACOBI_TRAFFIC["source_sha256_16"]):
+        roofline["traffic"] = JACOBI_TRAFFIC["bytes_per_launch"]
+        roofline["traffic_note"] = ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                    "this launch shape on this source (one-pass capture)")
     bytes_per_svd = algorithmic_bytes(case, R, plan.k, s_v)
     peaks = measured_peaks()
     hbm = {"algorithmic_bytes_per_svd": bytes_per_svd,
