@@ -562,6 +562,8 @@ def main():
     ap.add_argument("--serve-grace", type=float, default=2.0)
     ap.add_argument("--no-tune", action="store_true",
                     help="zipf_wide: skip the Jacobi launch-shape autotuner")
+    ap.add_argument("--jacobi-cluster", type=int, default=0,
+                    help="zipf_wide: CTAs per block matrix of the FP32 Jacobi (skips the autotuner)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -598,7 +600,9 @@ def main():
     va = torch.from_numpy(case.vals).to(dev)
     # launch shape of the FP32 Jacobi (CTAs per block matrix), measured
     tuned = None
-    if args.precision == "mixed" and not args.no_tune:
+    if args.jacobi_cluster > 0:
+        tuned = {"jacobi_cluster": args.jacobi_cluster, "note": "given on the command line"}
+    elif args.precision == "mixed" and not args.no_tune:
         from paper_2009_09767_gb300 import autotune
         cs, cs_ms = autotune.tune_cluster(case, device=dev)
         tuned = {"jacobi_cluster": cs, "block_jacobi_ms_by_cluster": cs_ms,
