@@ -1151,6 +1151,22 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
     const int nblk = np * (np + 1) / 2;
     const int rtiles = Mp / kB2;
     const int njobs = nblk + np * rtiles;
+    // The single-matrix form (a few update jobs per warp) takes its jobs
+    // longest first: block jobs (two products) go round robin, then each
+    // warp takes a run of column jobs (one product) that brings it to
+    // ceil(products / warps); round robin over all jobs would leave the warps
+    // with an extra block job two products above the rest, and every step
+    // waits for the slowest.  The staged form (a dozen jobs per warp) keeps
+    // round robin over all jobs, which measured faster there.
+    int nbw = 0, vstart = 0, nseq = 0;
+    if constexpr (!kSt) {
+        const int nvj = njobs - nblk;
+        const int qb = nblk / nwarps, rb = nblk % nwarps;
+        nbw = qb + (gwarp < rb ? 1 : 0);
+        const int cap = (2 * nblk + nvj + nwarps - 1) / nwarps;
+        for (int x = 0; x < gwarp; ++x) vstart += max(0, cap - 2 * (qb + (x < rb ? 1 : 0)));
+        nseq = nbw + max(0, min(cap - 2 * nbw, nvj - vstart));
+    }
     int sweep = 0;
     bool converged = false;
     while (sweep < max_sweeps) {
@@ -1217,13 +1233,10 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
             };
             // a block whose two rotations are the identity (or a tile whose
             // one is) does not change
-            auto next_job = [&](int j) {
-                for (; j < njobs; j += nwarps) {
-                    int u, w2, r0;
-                    const bool blk = decode(j, u, w2, r0);
-                    if (!(ident_of(u) && (!blk || ident_of(w2)))) break;
-                }
-                return j;
+            auto skip = [&](int j) {
+                int u, w2, r0;
+                const bool blk = decode(j, u, w2, r0);
+                return ident_of(u) && (!blk || ident_of(w2));
             };
             auto run_job = [&](bool blk, int u, int w2, int r0, const float2 (&op)[16]) {
                 int ui, uj;
@@ -1251,6 +1264,10 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                     if (blk) circle_pair(nb, step, w2, wi2, wj);
                     stage_rows(stg, blk ? G : V, Mp, ui, uj, blk, wi2, wj, r0);
                 };
+                auto next_job = [&](int j) {
+                    while (j < njobs && skip(j)) j += nwarps;
+                    return j;
+                };
                 int j = next_job(gwarp);
                 if (j < njobs) issue(j);
                 while (j < njobs) {
@@ -1269,9 +1286,9 @@ __device__ void jacobi4_matrix(float* __restrict__ G, float* __restrict__ V, int
                 }
             } else {
                 const float2 none[16] = {};
-                for (int j = gwarp; j < njobs; j += nwarps) {
+                for (int t = 0; t < nseq; ++t) {
                     int u, w2, r0;
-                    const bool blk = decode(j, u, w2, r0);
+                    const bool blk = decode(t < nbw ? gwarp + t * nwarps : nblk + vstart + (t - nbw), u, w2, r0);
                     if (ident_of(u) && (!blk || ident_of(w2))) continue;
                     run_job(blk, u, w2, r0, none);
                 }
