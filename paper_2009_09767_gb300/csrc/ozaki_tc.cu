@@ -1,6 +1,6 @@
 // ozaki_tc.cu -- the exact-slice FP64-accurate product (see ozaki.cu for the
 // splitting) on the fifth-generation tensor cores: operands brought into
-// shared memory by the tensor memory accelerator (cp.async.bulk.tensor, 128-
+// shared memory by the tensor memory accelerator (cp.async.bulk.tensor, 64-
 // byte swizzle), tcgen05.mma with FP32 accumulators in tensor memory (TMEM).
 //
 // C = alpha A B^T (+ beta C) from the S bf16 slices of A (m rows) and B
@@ -13,17 +13,15 @@
 // for bit that of the mma.sync kernel of ozaki.cu: both form the same
 // integers and convert them once.
 //
-// CTA: 128 threads, output tile 128 x 64 (row i of the tile = TMEM lane i =
-// thread i at the drain), S accumulators of 64 columns in one 512-column
-// TMEM allocation.  The product is bound by bringing the operand slices into
-// shared memory, so the tile is as wide as the accumulators allow (fewer
-// operand bytes per output) and k runs in stages of 32 through NBUF shared
-// buffers (three stages in flight for S = 5, five for S = 3).  A product
-// with fewer than two such tiles per SM (one 512 x 512 matrix) takes tiles
-// 128 x 32 instead, for twice the CTAs.  Warp 0 runs
+// CTA: 128 threads, output tile 128 x 32 (row i of the tile = TMEM lane i =
+// thread i at the drain), S accumulators of 32 columns in a 256-column TMEM
+// allocation, k in stages of 32 through NBUF shared buffers of about 108 KB
+// in all, so that two CTAs share an SM: one's drain and epilogue overlap
+// the other's copies and MMAs (a 128 x 64 tile, one CTA per SM with three
+// stages in flight, was 12% slower on the refinement's products).  Warp 0 runs
 // the pipeline (lane 0 issues): each stage's tensor copies (one per slice
 // and operand, completion counted in bytes on the buffer's "full" mbarrier)
-// and, once they have landed, the stage's MMAs (M = 128, N = 64, K = 16),
+// and, once they have landed, the stage's MMAs (M = 128, N = 32, K = 16),
 // committed to the buffer's "empty" mbarrier before the buffer is refilled;
 // the other warps wait for the drain.  Shared tiles are K-major with the
 // 64-byte swizzle: rows of 32 bf16, 8-row atoms of 512 bytes; the second
@@ -41,24 +39,22 @@ namespace rk {
 
 namespace {
 
-constexpr int TBM = 128, TBK = 32;
-constexpr uint32_t kTmemCols = 512;
+constexpr int TBM = 128, TBN = 32, TBK = 32;
+constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitCycles = 1ll << 31;        // ~1 s of SM clock before a wait gives up
 
-// TBN: tile width, 64 (fewer operand bytes per output) or 32 (twice the CTAs
-// for small products)
-template <int S, int TBN>
+template <int S>
 struct TcSmem {
     static constexpr int A_BYTES = TBM * TBK * 2;    // one slice tile, 8 KB
-    static constexpr int B_BYTES = TBN * TBK * 2;    // 4 or 2 KB
+    static constexpr int B_BYTES = TBN * TBK * 2;    // 2 KB
     static constexpr int STAGE = S * (A_BYTES + B_BYTES);
-    static constexpr int NBUF = (200 * 1024) / STAGE;
+    static constexpr int NBUF = (108 * 1024) / STAGE;  // two CTAs per SM
     static constexpr int BAR = NBUF * STAGE;         // barriers after the buffers
     static constexpr int BYTES = BAR + 256 + 1024;   // + barriers, TMEM slot, alignment slack
     // exact run of an accumulator: S pairs x k x 2^14 <= 2^24
     static constexpr int STAGES_PER_DRAIN = (1024 / S) / TBK;
     static_assert(S * TBN <= (int)kTmemCols, "accumulators fit the allocation");
-    static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
+    static_assert(2 * (BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -80,18 +76,15 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
 
 // instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
 // K-major, N = TBN, M = TBM
-template <int TBN>
-constexpr uint32_t idesc_f16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
-}
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                            ((uint32_t)(TBM >> 4) << 24);
 
-template <int TBN>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                           uint32_t accumulate) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc_f16<TBN>()), "r"(accumulate));
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
@@ -163,14 +156,14 @@ __device__ __forceinline__ int tc_exp(unsigned long long bits) {
     return (ef == 0 ? 1 : ef) - 1022;
 }
 
-template <int S, int TBN>
-__global__ void __launch_bounds__(128, 1)
+template <int S>
+__global__ void __launch_bounds__(128, 2)
 k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m,
           int n, int64_t kpad, int64_t kc, const unsigned long long* __restrict__ amaxA,
           int rowsA_pad, const unsigned long long* __restrict__ amaxB, int rowsB_pad,
           double alpha, double beta, double* __restrict__ C, int64_t ldc, int64_t strideC,
           int64_t strideSplit, int nsplit, int sym, int* __restrict__ err) {
-    using L = TcSmem<S, TBN>;
+    using L = TcSmem<S>;
     constexpr int NB = L::NBUF;
     const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
     if (sym && j0 + TBN - 1 < i0) return;   // below the diagonal: mirrored from above
@@ -265,7 +258,7 @@ k_oz_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                             const int q = a + bs - 2;
 #pragma unroll
                             for (int kk = 0; kk < TBK / 16; ++kk)
-                                umma_bf16<TBN>(tbase + (uint32_t)(q * TBN),
+                                umma_bf16(tbase + (uint32_t)(q * TBN),
                                           dA + (uint64_t)(((a - 1) * L::A_BYTES + kk * 32) >> 4),
                                           dB + (uint64_t)(((bs - 1) * L::B_BYTES + kk * 32) >> 4),
                                           (kk == 0 && a == 1) ? first : 1u);
@@ -386,39 +379,23 @@ cudaError_t slice_map(CUtensorMap* map, const OzOperand& op, int nb, int box_row
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int S, int TBN>
+template <int S>
 cudaError_t umma_gemm_t(int nb, int m, int n, int64_t kpad, int nsplit, const OzOperand& A,
                         const OzOperand& B, double alpha, double beta, double* C, int64_t ldc,
                         int64_t strideC, int64_t strideSplit, int sym, int* err, cudaStream_t s) {
-    constexpr int smem = TcSmem<S, TBN>::BYTES;
+    constexpr int smem = TcSmem<S>::BYTES;
     CUtensorMap ta, tb;
     RK_CUDA_TRY(slice_map(&ta, A, nb, TBM));
     RK_CUDA_TRY(slice_map(&tb, B, nb, TBN));
-    RK_CUDA_TRY(cudaFuncSetAttribute(k_oz_umma<S, TBN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RK_CUDA_TRY(cudaFuncSetAttribute(k_oz_umma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // split chunks on stage boundaries: a tensor copy past a chunk's end would
     // read the next chunk (past kpad it reads zeros)
     const int64_t kc = round_up(ceil_div(kpad, nsplit), TBK);
     dim3 grid((unsigned)ceil_div(n, TBN), (unsigned)ceil_div(m, TBM), (unsigned)(nb * nsplit));
-    k_oz_umma<S, TBN><<<grid, 128, smem, s>>>(ta, tb, m, n, kpad, kc, A.amax, A.rows_pad, B.amax,
-                                              B.rows_pad, alpha, beta, C, ldc, strideC, strideSplit,
-                                              nsplit, sym, err);
+    k_oz_umma<S><<<grid, 128, smem, s>>>(ta, tb, m, n, kpad, kc, A.amax, A.rows_pad, B.amax,
+                                         B.rows_pad, alpha, beta, C, ldc, strideC, strideSplit,
+                                         nsplit, sym, err);
     return cudaGetLastError();
-}
-
-// the wide tile unless that leaves fewer than two CTAs per SM
-template <int S>
-cudaError_t umma_gemm_s(int nb, int m, int n, int64_t kpad, int nsplit, const OzOperand& A,
-                        const OzOperand& B, double alpha, double beta, double* C, int64_t ldc,
-                        int64_t strideC, int64_t strideSplit, int sym, int* err, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    RK_CUDA_TRY(cudaGetDevice(&dev));
-    RK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t wide = ceil_div(n, 64) * ceil_div(m, TBM) * (int64_t)nb * nsplit;
-    if (wide >= 2 * (int64_t)sms)
-        return umma_gemm_t<S, 64>(nb, m, n, kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
-                                  strideSplit, sym, err, s);
-    return umma_gemm_t<S, 32>(nb, m, n, kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
-                              strideSplit, sym, err, s);
 }
 
 }  // namespace
@@ -428,14 +405,14 @@ cudaError_t launch_oz_gemm_tc(int nb, int m, int n, const OzOperand& A, const Oz
                               int sym, cudaStream_t s, int nsplit, int64_t strideSplit, int* err) {
     if (A.S != B.S || A.kpad != B.kpad || m > A.rows_pad || n > B.rows_pad || nsplit < 1)
         return cudaErrorInvalidValue;
-    if (A.rows_pad % TBM != 0 || B.rows_pad % 64 != 0 || A.kpad % TBK != 0)
+    if (A.rows_pad % TBM != 0 || B.rows_pad % TBN != 0 || A.kpad % TBK != 0)
         return cudaErrorInvalidValue;
     if (sym && m != n) return cudaErrorInvalidValue;
     if (nb <= 0 || m <= 0 || n <= 0) return cudaSuccess;
     if (A.S == 3)
-        return umma_gemm_s<3>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
+        return umma_gemm_t<3>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC,
                               strideSplit, sym, err, s);
-    return umma_gemm_s<5>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC, strideSplit,
+    return umma_gemm_t<5>(nb, m, n, A.kpad, nsplit, A, B, alpha, beta, C, ldc, strideC, strideSplit,
                           sym, err, s);
 }
 

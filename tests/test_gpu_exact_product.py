@@ -7,8 +7,7 @@ Two independent checks:
     same exact integer sums and convert them once, so their results must be
     equal bit for bit, whatever the shapes (ragged m, n, k; k above the
     1024-deep exact run, so several accumulator drains; one slice count and
-    the other; the symmetric form; the narrow tiles of small products and the
-    wide tiles of large ones);
+    the other; the symmetric form; grids of under and over two CTAs per SM);
   * against the FP64 product A B^T computed by numpy, the error stays within
     the splitting's bound 2^(3 - 8 S) k 2^(e_i + e_j) (e_i: the exponent bound
     of row i), with rows spanning six orders of magnitude and a zero row.
@@ -48,7 +47,7 @@ CASES = [  # m, n, k, slices
     (128, 32, 64, 5), (200, 77, 300, 5), (512, 512, 512, 5), (300, 130, 2500, 5),
     (64, 96, 40, 3), (1, 1, 1, 5), (257, 33, 1031, 3), (130, 500, 4096, 5),
     (200, 256, 1100, 3),
-    # enough tiles for the wide (128 x 64) tile: 2 CTAs per SM or more
+    # grids of several hundred tiles (two CTAs per SM share the device)
     (2048, 2048, 512, 5), (1100, 2300, 600, 3),
 ]
 
