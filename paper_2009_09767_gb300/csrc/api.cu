@@ -124,7 +124,7 @@ struct svd_plan_s {
     int32_t* rr_csize = nullptr;
     int32_t* rr_ncl = nullptr;
     int32_t* rr_cid = nullptr;
-    int32_t* rr_rowexp = nullptr;
+    int32_t* rr_rowmax = nullptr;
 
     // svd_run_host staging (lazily allocated)
     char* host_arena = nullptr;
@@ -297,7 +297,7 @@ void carve(svd_plan_s* p, Carver& c) {
         p->rr_csize = c.take<int32_t>((size_t)(D + 1) * (Mp / 2));
         p->rr_ncl = c.take<int32_t>(D + 1);
         p->rr_cid = c.take<int32_t>((size_t)(D + 1) * Mp);
-        p->rr_rowexp = c.take<int32_t>((size_t)(D + 1) * Mp);
+        p->rr_rowmax = c.take<int32_t>((size_t)(D + 1) * Mp);
     }
 }
 
@@ -307,7 +307,7 @@ RRWork rr_work(svd_plan_s* p, int first) {
     const int Mp = p->Mp;
     return RRWork{p->rr_order + (size_t)first * Mp, p->rr_cstart + (size_t)first * (Mp / 2),
                   p->rr_csize + (size_t)first * (Mp / 2), p->rr_ncl + first,
-                  p->rr_cid + (size_t)first * Mp, p->rr_rowexp + (size_t)first * Mp, p->rr_kappa,
+                  p->rr_cid + (size_t)first * Mp, p->rr_rowmax + (size_t)first * Mp, p->rr_kappa,
                   p->M, 0};
 }
 

@@ -61,39 +61,57 @@ __device__ __forceinline__ void rr_pair(int n, int r, int u, int& a, int& b) {
     if (a > b) { const int t = a; a = b; b = t; }
 }
 
-// rowexp[a]: 2^rowexp[a] > max_{c != a} |S_ac| + |lam_c| |B_ac| with
-// lam_c = S_cc / B_cc, from IEEE exponent fields alone (the FP64 pipe, a
-// small fraction of the others' rate, stays idle): with e(x) the biased
-// exponent, |x| < 2^(e(x) - 1022) and |S_cc / B_cc| < 2^(e(S_cc) - e(B_cc) + 1),
-// so the bound is at most 8x the maximum.  A CTA of 8 warps takes 32 rows
-// of one matrix, a warp a row at a time.
-__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+// rowmax[a] >= max_{c != a} |S_ac| + |lam_c| |B_ac| (lam_c = S_cc / B_cc) as
+// FP32 bits, from the high words of the FP64 entries and FP32 arithmetic
+// rounded upwards: within about 4e-6 of the exact maximum, and never below
+// it.  The FP64 pipe (a small fraction of the others' rate) stays idle.  A
+// CTA of 8 warps takes 32 rows of one matrix, a warp a row at a time.
+//
+// |x| from its high word: the FP32 number with x's exponent and the top 20
+// bits of its mantissa; one unit of the 20th bit more is an upper bound,
+// the truncation itself a lower one.  Outside FP32's normal range: 2^-126
+// (upper) or 0 (lower) below it, infinity (upper) or FLT_MAX (lower) above.
+__device__ __forceinline__ float hi_abs_upper(double x) {
+    const int h = __double2hiint(x) & 0x7fffffff;
+    const int e = h >> 20;                       // biased FP64 exponent
+    if (e >= 1151) return __int_as_float(0x7f800000);
+    if (e < 897) return 0x1p-126f;
+    return __uint_as_float((((unsigned)(e - 896) << 23) | ((unsigned)(h & 0xfffff) << 3)) + 8u);
+}
+__device__ __forceinline__ float hi_abs_lower(double x) {
+    const int h = __double2hiint(x) & 0x7fffffff;
+    const int e = h >> 20;
+    if (e >= 1151) return FLT_MAX;
+    if (e < 897) return 0.0f;
+    return __uint_as_float(((unsigned)(e - 896) << 23) | ((unsigned)(h & 0xfffff) << 3));
+}
 
 __global__ void __launch_bounds__(256)
-k_rr_rowexp(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp,
-            int32_t* __restrict__ rowexp) {
-    __shared__ int elam[kMaxM];     // |lam_c| < 2^(elam[c] - 1022)
+k_rr_rowmax(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp,
+            int32_t* __restrict__ rowmax) {
+    __shared__ float lamb[kMaxM];     // >= |lam_c|
     const int b = blockIdx.y;
     const int64_t mm = (int64_t)Mp * Mp;
     const double* Sb = S + b * mm;
     const double* Bb = B + b * mm;
     for (int c = threadIdx.x; c < M; c += blockDim.x) {
-        // a zero or subnormal B_cc leaves no bound: scan the whole row
-        const int eb = exp_field(Bb[(int64_t)c * Mp + c]);
-        elam[c] = eb == 0 ? 4095 : exp_field(Sb[(int64_t)c * Mp + c]) - eb + 1023;
+        // a zero or tiny B_cc leaves no bound: the row's scan is unlimited
+        const float bl = hi_abs_lower(Bb[(int64_t)c * Mp + c]);
+        lamb[c] = bl > 0.0f ? __fdiv_ru(hi_abs_upper(Sb[(int64_t)c * Mp + c]), bl)
+                            : __int_as_float(0x7f800000);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int a = blockIdx.x * 32 + warp; a < min(M, blockIdx.x * 32 + 32); a += 8) {
         const double* Sa = Sb + (int64_t)a * Mp;
         const double* Ba = Bb + (int64_t)a * Mp;
-        int m = -4096;
+        float m = 0.0f;
         for (int c = lane; c < M; c += 32) {
             if (c == a) continue;
-            m = max(m, max(exp_field(Sa[c]) - 1021, elam[c] + exp_field(Ba[c]) - 2043));
+            m = fmaxf(m, __fadd_ru(hi_abs_upper(Sa[c]), __fmul_ru(lamb[c], hi_abs_upper(Ba[c]))));
         }
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) rowexp[(int64_t)b * Mp + a] = m;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) rowmax[(int64_t)b * Mp + a] = __float_as_int(m);
     }
 }
 
@@ -106,7 +124,7 @@ k_rr_rowexp(const double* __restrict__ S, const double* __restrict__ B, int M, i
 // kRRMax at their largest gaps.  cid[i] = the piece of index i, -1 outside
 // every piece.
 // One CTA of 1024 threads per matrix (Mp <= 1024).  The scan limit of row a
-// is 2^rowexp[a] (k_rr_rowexp), at least the exact maximum of the link
+// is kappa rowmax[a] (k_rr_rowmax), at least the exact maximum of the link
 // test's right-hand side over the row: pairs beyond the exact maximum fail
 // the test anyway, so the clusters are those of the exact limit.  The scan
 // runs a warp per position, 32 candidates per ballot, with the exact FP64
@@ -115,11 +133,11 @@ __global__ void __launch_bounds__(1024)
 k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int Mp, double kappa,
           int stagger, double* __restrict__ lam, double* __restrict__ lmax_out,
           int32_t* __restrict__ order, int32_t* __restrict__ cstart, int32_t* __restrict__ csize,
-          int32_t* __restrict__ ncl, int32_t* __restrict__ cid, const int32_t* __restrict__ rowexp_g) {
+          int32_t* __restrict__ ncl, int32_t* __restrict__ cid, const int32_t* __restrict__ rowmax_g) {
     __shared__ double key[kMaxM];
     __shared__ int id[kMaxM];
     __shared__ int reach[kMaxM];
-    __shared__ int rowexp[kMaxM];
+    __shared__ float rowmax[kMaxM];
     __shared__ double wmax[32];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int64_t mm = (int64_t)Mp * Mp;
@@ -132,7 +150,7 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         const double bii = Bb[(int64_t)i * Mp + i];
         const double l = bii > 0.0 ? Sb[(int64_t)i * Mp + i] / bii : 0.0;
         L[i] = l;
-        rowexp[i] = rowexp_g[(int64_t)b * Mp + i];
+        rowmax[i] = __int_as_float(rowmax_g[(int64_t)b * Mp + i]);
         cb[i] = -1;
         if (l == l) lm = fmax(lm, fabs(l));
     }
@@ -177,7 +195,7 @@ k_rr_plan(const double* __restrict__ S, const double* __restrict__ B, int M, int
         const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
         for (int q = warp; q < M; q += nw) {
             const int a = id[q];
-            const double lim = kappa * ldexp(1.0, rowexp[a]);    // no pair further than this links
+            const double lim = kappa * (double)rowmax[a];    // no pair further than this links
             const double* Sa = Sb + (int64_t)a * Mp;
             const double* Ba = Bb + (int64_t)a * Mp;
             int r = q;
@@ -575,10 +593,10 @@ cudaError_t launch_cluster_rr(const RRWork& w, int nmat, int Mp, double* X, doub
                               double* Tg, double* lam, double* lmax, cudaStream_t s) {
     if (nmat <= 0) return cudaSuccess;
     if (Mp > kMaxM || Mp % kRRTile != 0 || w.M > Mp) return cudaErrorInvalidValue;
-    k_rr_rowexp<<<dim3((unsigned)ceil_div(w.M, 32), nmat), 256, 0, s>>>(S, B, w.M, Mp, w.rowexp);
+    k_rr_rowmax<<<dim3((unsigned)ceil_div(w.M, 32), nmat), 256, 0, s>>>(S, B, w.M, Mp, w.rowmax);
     RK_CUDA_TRY(cudaGetLastError());
     k_rr_plan<<<nmat, 1024, 0, s>>>(S, B, w.M, Mp, w.kappa, w.stagger, lam, lmax, w.order,
-                                    w.cstart, w.csize, w.ncl, w.cid, w.rowexp);
+                                    w.cstart, w.csize, w.ncl, w.cid, w.rowmax);
     RK_CUDA_TRY(cudaGetLastError());
     const int smem = (int)rr_smem_bytes();
     RK_CUDA_TRY(cudaFuncSetAttribute(k_rr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -150,7 +150,7 @@ struct RRWork {
     int32_t* csize;
     int32_t* ncl;
     int32_t* cid;      // per matrix, Mp: cluster of each index (-1: none)
-    int32_t* rowexp;   // per matrix, Mp: exponent bound of each row's link test
+    int32_t* rowmax;   // per matrix, Mp: FP32 upper bound of each row's link test (bits)
     double kappa;      // pairs whose first-order mixing estimate is >= 1/kappa are clustered
     int M;             // indices >= M are padding and never clustered
     int stagger = 0;   // odd refinement steps: long runs are cut half a piece later
