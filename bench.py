@@ -146,7 +146,7 @@ class ClockSampler:
 # zipf_wide SVD (25,573,739,008 + 38,630,312,960 bytes in 24.34 ms), with the hash of
 # the kernel source it was taken on.  The line reports it (labelled as stored) only for
 # that launch shape and while the source is unchanged.
-JACOBI_TRAFFIC = {"source_sha256_16": "6e8482a0ec258288", "blocks": 64,
+JACOBI_TRAFFIC = {"source_sha256_16": "01b83a6bd1e480c5", "blocks": 64,
                   "bytes_per_launch": 25_573_739_008 + 38_630_312_960}
 
 

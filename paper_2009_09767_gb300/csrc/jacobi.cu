@@ -508,9 +508,9 @@ k_jacobi_items(const JacobiItem* __restrict__ items, int nitems, int* __restrict
 // new matrix is made of the 32 x 32 blocks
 //   G'[P_u, P_w] = Q_u^T G[P_u, P_w] Q_w          (u <= w, mirrored below)
 // and the eigenvector columns V'[:, P_u] = V[:, P_u] Q_u (V = Vt^T while the
-// solve runs).  Every block is one independent warp job: no shared-memory
-// staging and no CTA-wide barrier inside the update, one barrier after the
-// pair solves (their Q are published through L2) and one after the update.
+// solve runs).  Every block is one independent warp job, with no CTA-wide
+// barrier inside the update: one cluster barrier after the pair solves
+// (their Q are published through L2) and one after the update.
 //
 // Products run on the tensor cores with f16 operands split as
 // hi = f16(x), lo = f16(x - hi) and accumulated as lo*hi + hi*lo + hi*hi
