@@ -179,7 +179,10 @@ typedef struct {
 typedef struct svd_plan_s* svd_plan_t;
 
 /* Validate desc, allocate the plan and its device workspace (owned by the
- * plan until svd_free).  *device_bytes_needed (may be NULL) receives the
+ * plan until svd_free).  The plan fixes what section III's Algorithm 1
+ * needs before it reads A: the shape, the D column blocks of the split
+ * (floor(N/D) columns each, the remainder in the last, or explicit bounds),
+ * the rank fix (Algorithms 2-4, or TRUNCATE) and the precision.  *device_bytes_needed (may be NULL) receives the
  * workspace size.  Returns SVD_ERR_INVALID_ARG / SVD_ERR_UNSUPPORTED /
  * SVD_ERR_OOM without allocating anything on failure. */
 svd_status svd_plan(const svd_desc* desc, svd_plan_t* out, size_t* device_bytes_needed);
@@ -192,7 +195,11 @@ svd_status svd_plan_ws(const svd_desc* desc, void* d_workspace, size_t workspace
 /* Workspace size for desc without allocating (for admission control). */
 svd_status svd_plan_bytes(const svd_desc* desc, size_t* device_bytes_needed);
 
-/* Enqueue one SVD of the CSC matrix on `stream`.
+/* Enqueue one SVD of the CSC matrix on `stream`: section III of the paper
+ * for one matrix.  Algorithm 1's split and lonely-node scan, the rank fix
+ * (Algorithms 2-4), the block cross products A^i A^i^T (Eq. 2) and their
+ * eigensolves (the block SVDs of Eq. 1), the proxy P and the eigensolve of
+ * P P^T (Eqs. 2-3), then V = A'^T U S^-1 (left to future work in section V).
  *   d_sigma   double[k]            singular values, descending
  *   d_U       double[M*k]          column-major left vectors
  *   d_V       float[N*k] (MIXED) or double[N*k] (FP64), row-major right
@@ -208,7 +215,7 @@ svd_status svd_run(svd_plan_t plan, const int64_t* d_col_ptr, const int32_t* d_r
                    int32_t* d_rank, svd_patch* d_patches, int64_t* d_npatches,
                    void* stream);
 
-/* Same computation from HOST buffers: copies the CSC to plan-owned device
+/* Same computation (section III) from HOST buffers: copies the CSC to plan-owned device
  * memory, runs, and copies sigma, U, V (unless SVD_FLAG_SKIP_V or h_V ==
  * NULL), rank and patches back.  Synchronous; pinned host memory makes the
  * copies fast but is not required.  When h_V is page-locked (cudaHostAlloc,
@@ -219,7 +226,10 @@ svd_status svd_run_host(svd_plan_t plan, const int64_t* h_col_ptr, const int32_t
                         int32_t* h_rank, svd_patch* h_patches, int64_t* h_npatches,
                         void* stream);
 
-/* Wait for the plan's last run and return its device-detected status. */
+/* Wait for the plan's last run and return its device-detected status: a
+ * Jacobi eigensolve of a block or of P P^T that used max_sweeps
+ * (SVD_ERR_NOT_CONVERGED), or a bounded wait of the tensor-core product
+ * that ran out (SVD_ERR_TIMEOUT). */
 svd_status svd_sync(svd_plan_t plan);
 
 /* Synchronous CSC validation (structure only): col_ptr monotone and ending at
@@ -227,7 +237,8 @@ svd_status svd_sync(svd_plan_t plan);
 svd_status svd_check_csc(int32_t M, int64_t N, int64_t nnz, const int64_t* d_col_ptr,
                          const int32_t* d_row_idx, void* stream);
 
-/* Copy an intermediate of the last run to host memory (after svd_sync).
+/* Copy an intermediate of the last run to host memory (after svd_sync):
+ * the quantities of Algorithm 1 and Eqs. 1-3 named below.
  * `bytes` must equal the item's size; returns SVD_ERR_INVALID_ARG otherwise. */
 enum {
     SVD_Q_BLOCK_BOUNDS = 1,  /* int64[D+1] column boundaries (Algorithm 1 split) */
@@ -251,7 +262,8 @@ enum {
 };
 svd_status svd_query(svd_plan_t plan, int32_t what, int64_t index, void* h_dst, size_t bytes);
 
-/* ---- Batches: many plans in one pass (all plans' block eigensolves in one
+/* ---- Batches (no counterpart in the paper: svd_run's section III
+ * computation for many matrices): many plans in one pass (all plans' block eigensolves in one
  * persistent launch, likewise the merge eigensolves; the per-matrix stages on
  * a pool of worker streams).  Each plan keeps its own workspace; the batch
  * object adds the work lists, streams and (optionally) a CUDA graph. */
@@ -285,7 +297,8 @@ svd_status svd_batch_sync(svd_batch_t batch);
 int64_t svd_batch_launches(svd_batch_t batch);
 void svd_batch_free(svd_batch_t batch);
 
-/* ---- Serving: a continuous-batching SVD service on one GPU.  A scheduler
+/* ---- Serving (no counterpart in the paper: svd_run's section III
+ * computation for requests that arrive over time): a continuous-batching SVD service on one GPU.  A scheduler
  * thread admits submitted requests in arrival order as stream slots and room
  * in the device-memory budget free up; each admitted request gets its plan
  * workspace, CSC and outputs from one pool allocation inside the budget and
