@@ -489,6 +489,8 @@ def run_single_case(args):
     else:
         c = synth.small_uniform().with_values(np.float32)
         bounds, k = None, 0
+    if args.legacy_mma:
+        flags |= rk.FLAG_LEGACY_MMA
     p = rk.Plan(c.M, c.N, c.nnz, c.num_blocks, value_type="f32", precision=args.precision,
                 bounds=bounds, k=k, flags=flags, rank_fix=args.rank_fix,
                 seed=args.seed)
@@ -517,6 +519,7 @@ def run_single_case(args):
             "config": {"workload": f"{c.name} M={c.M} N={c.N} nnz={c.nnz} D={c.num_blocks} "
                                    f"k={p.k}", "precision": args.precision,
                        "rank_fix": args.rank_fix, "insertions": int(o["npatches"].item()),
+                       "products": "mma.sync" if args.legacy_mma else "tcgen05",
                        "lonely_nodes": int(p.query(rk.Q_LONELY).sum())},
             "stage_ms": {n: float(totals[i] / max(totals[-1], 1)) for i, n in enumerate(rk.STAGES)},
             "sweeps": p.query(rk.Q_SWEEPS).tolist()[-1], "rank": int(o["rank"].item()),
@@ -552,6 +555,8 @@ def main():
                     choices=["truncate", "random", "neighbor", "neighbor_random"],
                     help="large/small: rank fix (Algorithms 2-4); the headline is truncate")
     ap.add_argument("--seed", type=int, default=1, help="rank-fix key")
+    ap.add_argument("--legacy-mma", action="store_true",
+                    help="large/small/tall: exact-slice products on mma.sync instead of tcgen05")
     ap.add_argument("--no-plain", action="store_true",
                     help="zipf_wide: skip the plain FP64 arm (same matrix, --precision fp64)")
     ap.add_argument("--no-serve", action="store_true",
