@@ -122,6 +122,31 @@ def test_tall_plan_bytes_validation(lib):
                           [96]})[0] == 1
 
 
+def test_tree_plan_bytes(lib):
+    """The tree merge (section II's multi-level proxy merge) never forms the
+    one-level proxy P (M x R, R up to D*M): at the large workload's shape the
+    tree plan needs at least M*M*D*8 bytes less than the one-level plan, for
+    every D, and its size does not grow with the number of levels (arity)."""
+    for D in (64, 256, 512):
+        kw = dict(M=1024, N=8_000_000, nnz=80_000_000, num_blocks=D, k=100, precision="mixed")
+        st, flat = _bytes(lib, **kw)
+        assert st == 0
+        trees = []
+        for arity in (2, 4, 16):
+            st, t = _bytes(lib, **kw, merge_arity=arity)
+            assert st == 0
+            trees.append(t)
+        assert flat - trees[0] >= 1024 * 1024 * D * 8
+        assert len(set(trees)) == 1
+        # a per-node rank cap k' >= k changes nothing in the workspace either
+        assert _bytes(lib, **kw, merge_arity=4, merge_rank=200) == (0, trees[0])
+    small = dict(M=64, N=4096, nnz=100, num_blocks=4, k=32)
+    # arity 0 and 1 are the one-level merge of section III
+    assert _bytes(lib, **small, merge_arity=1) == _bytes(lib, **small)
+    for kw in ({"merge_arity": -1}, {"merge_rank": -1}, {"merge_rank": 31}):
+        assert _bytes(lib, **small, **kw)[0] == 1, kw
+
+
 def test_null_plan_is_rejected(lib):
     assert lib.svd_sync(None) == 1
     assert lib.svd_query(None, 1, 0, None, 0) == 1
